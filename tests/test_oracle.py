@@ -1,0 +1,295 @@
+"""Pins for the CPU oracle against facts the mathematics and the paper fix.
+
+None of these re-types the oracle's loop: each compares it with an independent
+route (dense matrix products, algebraic identities, closed forms, brute force
+on tiny inputs) chosen so that a dropped term, a wrong index, a transposed
+operand or a wrong summation order fails at least one of them."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_00844_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense(M):
+    D = np.zeros((M.nrows, M.ncols), dtype=np.float64 if M.val is None or
+                 np.issubdtype(np.asarray(M.val).dtype, np.floating) else np.int64)
+    rows = np.repeat(np.arange(M.nrows), np.diff(M.rowptr))
+    D[rows, np.asarray(M.col, dtype=np.int64)] = 1 if M.val is None else M.val
+    return D
+
+
+def pattern(M):
+    P = np.zeros((M.nrows, M.ncols), dtype=bool)
+    rows = np.repeat(np.arange(M.nrows), np.diff(M.rowptr))
+    P[rows, np.asarray(M.col, dtype=np.int64)] = True
+    return P
+
+
+def assert_valid_csr(C):
+    rp = np.asarray(C.rowptr)
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == len(C.col)
+    for i in range(C.nrows):
+        c = np.asarray(C.col[rp[i]:rp[i + 1]])
+        assert np.all(np.diff(c) > 0), f"row {i} not strictly ascending"
+        assert c.size == 0 or (c[0] >= 0 and c[-1] < C.ncols)
+
+
+SHAPES = [(1, 1, 1), (5, 1, 7), (1, 9, 1), (13, 17, 11), (32, 20, 40), (64, 64, 64), (3, 50, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("density", [0.02, 0.15, 0.5])
+def test_integer_values_equal_dense_matmul(shape, density):
+    m, l, n = shape
+    seed = hash((shape, density)) % 2**31
+    A = inputs.random_csr(m, l, density, seed, value="int", empty_rows=0.2)
+    B = inputs.random_csr(l, n, density, seed + 1, value="int", empty_rows=0.2)
+    C = oracle.spgemm(A, B)
+    assert_valid_csr(C)
+    # pattern = structural product (explicit zeros and cancellations kept)
+    P = (pattern(A).astype(np.int64) @ pattern(B).astype(np.int64)) > 0
+    assert np.array_equal(pattern(C), P)
+    # values = exact integer dense product on the pattern
+    D = dense(A) @ dense(B)
+    assert np.array_equal(dense(C)[P], D[P])
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_float_values_close_to_dense_matmul(shape):
+    m, l, n = shape
+    A = inputs.random_csr(m, l, 0.3, 7, value="u01_f64")
+    B = inputs.random_csr(l, n, 0.3, 8, value="u01_f64")
+    C = oracle.spgemm(A, B)
+    D = dense(A) @ dense(B)
+    np.testing.assert_allclose(dense(C), D, rtol=1e-13, atol=0)
+
+
+def brute_force(A, B):
+    """Triple loop in pure Python over dense copies; sum in ascending k,
+    first structural product starts the sum."""
+    dA, dB = pattern(A), pattern(B)
+    vA, vB = dense(A), dense(B)
+    out = {}
+    for i in range(A.nrows):
+        for j in range(B.ncols):
+            acc = None
+            for k in range(A.ncols):
+                if dA[i, k] and dB[k, j]:
+                    p = float(vA[i, k]) * float(vB[k, j])
+                    acc = p if acc is None else acc + p
+            if acc is not None:
+                out[(i, j)] = acc
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bitexact_against_brute_force_ascending_k(seed):
+    A = inputs.random_csr(9, 12, 0.4, 100 + seed, value="u01_f64")
+    B = inputs.random_csr(12, 10, 0.4, 200 + seed, value="u01_f64")
+    ref = brute_force(A, B)
+    C = oracle.spgemm(A, B)
+    got = {}
+    for i in range(C.nrows):
+        for t in range(C.rowptr[i], C.rowptr[i + 1]):
+            got[(i, int(C.col[t]))] = float(C.val[t])
+    assert got.keys() == ref.keys()
+    for key in ref:
+        assert got[key] == ref[key], key      # same order -> same bits
+
+
+def test_explicit_zeros_stay_in_pattern():
+    # row 0 of A = [1, 1], B = [[1],[-1]] -> C(0,0) = 0 but structurally present
+    A = inputs.CSR(1, 2, np.array([0, 2]), np.array([0, 1]), np.array([1.0, 1.0]))
+    B = inputs.CSR(2, 1, np.array([0, 1, 2]), np.array([0, 0]), np.array([1.0, -1.0]))
+    C = oracle.spgemm(A, B)
+    assert C.nnz == 1 and C.val[0] == 0.0
+    Z = inputs.CSR(1, 2, np.array([0, 2]), np.array([0, 1]), np.array([0.0, 0.0]))
+    assert oracle.spgemm(Z, B).nnz == 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_transpose_identity_bitexact(seed):
+    A = inputs.random_csr(30, 25, 0.2, seed, value="u01_f64")
+    B = inputs.random_csr(25, 35, 0.2, seed + 50, value="u01_f64")
+    C = oracle.spgemm(A, B)
+    Ct = oracle.transpose(C)
+    D = oracle.spgemm(oracle.transpose(B), oracle.transpose(A))
+    assert np.array_equal(Ct.rowptr, D.rowptr)
+    assert np.array_equal(Ct.col, D.col)
+    assert np.array_equal(Ct.val, D.val)      # same k order, b*a == a*b
+
+
+def test_identity_products_bitexact():
+    A = inputs.random_csr(40, 33, 0.1, 3, value="u01_f64")
+    for C in (oracle.spgemm(A, inputs.identity(33)), oracle.spgemm(inputs.identity(40), A)):
+        assert np.array_equal(C.rowptr, A.rowptr)
+        assert np.array_equal(C.col, A.col)
+        assert np.array_equal(C.val, A.val)
+
+
+@pytest.mark.parametrize("gen", ["er", "rmat", "random"])
+def test_nnz_bounds(gen):
+    if gen == "er":
+        A = inputs.er_column_regular(512, 8, 1)
+        B = A
+    elif gen == "rmat":
+        A = inputs.rmat(10)
+        B = A
+    else:
+        A = inputs.random_csr(50, 60, 0.05, 4)
+        B = inputs.random_csr(60, 70, 0.05, 5)
+    C = oracle.spgemm(A, B)
+    fl = oracle.row_flops(A, B)
+    cnt = np.diff(C.rowptr)
+    assert C.nnz <= fl.sum()
+    assert np.all(cnt <= np.minimum(fl, B.ncols))
+    lenB = np.diff(B.rowptr)
+    for i in range(A.nrows):
+        ks = np.asarray(A.col[A.rowptr[i]:A.rowptr[i + 1]], dtype=np.int64)
+        if ks.size:
+            assert cnt[i] >= lenB[ks].max()
+    # flops by an independent route: dense pattern products count multiplications
+    np.testing.assert_array_equal(
+        fl, (pattern(A).astype(np.int64) @ lenB.reshape(-1, 1)).ravel())
+
+
+def test_complete_graph_closed_forms():
+    with open(os.path.join(GOLDEN, "kn_trace.txt")) as fh:
+        rows = [tuple(map(int, ln.split())) for ln in fh if ln.strip() and not ln.startswith("#")]
+    for n, tr in rows:
+        K = inputs.complete_graph(n)
+        K2 = oracle.spgemm(K, K)
+        D2 = dense(K2)
+        # A^2 = (n-2) A + (n-1) I on K_n
+        expect = (n - 2) * (1 - np.eye(n)) + (n - 1) * np.eye(n)
+        assert np.array_equal(D2, expect)
+        K3 = oracle.spgemm(K2, K)
+        assert np.trace(dense(K3)) == tr == n * (n - 1) * (n - 2)
+
+
+def test_column_stochastic_products_stay_stochastic():
+    M = inputs.mcl_transition(9)                       # rows of M^T sum to 1
+    P = oracle.spgemm(M, M)                            # (M M)^T = M^T M^T
+    rs = np.add.reduceat(P.val, P.rowptr[:-1])
+    q = np.diff(M.rowptr).max() ** 2                   # terms per row sum
+    u = 2.0 ** -53
+    assert np.all(np.abs(rs - 1.0) <= 2 * q * u)
+
+
+def test_permutation_equivariance():
+    A = inputs.rmat(9, permute=False)
+    perm = inputs.permutation(A.nrows, 11)
+    C = oracle.spgemm(A, A)
+    PA = inputs.permute_symmetric(A, perm)
+    PC = oracle.spgemm(PA, PA)
+    ref = inputs.permute_symmetric(inputs.CSR(C.nrows, C.ncols, C.rowptr, C.col, C.val), perm)
+    assert np.array_equal(PC.rowptr, ref.rowptr)
+    assert np.array_equal(PC.col, ref.col)
+    np.testing.assert_allclose(PC.val, ref.val, rtol=1e-12)
+
+
+def test_boolean_pattern_equals_structural_pattern():
+    A = inputs.rmat(9)
+    Cb = oracle.spgemm(A.pattern(), A.pattern(), semiring="or_and")
+    Cf = oracle.spgemm(A, A)
+    assert Cb.val is None
+    assert np.array_equal(Cb.rowptr, Cf.rowptr)
+    assert np.array_equal(Cb.col, Cf.col)
+
+
+def test_int64_wraparound():
+    big = np.int64(2**62 + 12345)
+    A = inputs.CSR(1, 2, np.array([0, 2]), np.array([0, 1]), np.array([big, 3], dtype=np.int64))
+    B = inputs.CSR(2, 1, np.array([0, 1, 2]), np.array([0, 0]), np.array([4, big], dtype=np.int64))
+    C = oracle.spgemm(A, B)
+    expect = (int(big) * 4 + 3 * int(big)) % 2**64
+    if expect >= 2**63:
+        expect -= 2**64
+    assert int(C.val[0]) == expect
+
+
+def galerkin_closed_form(N, level):
+    """R^T A R at level l of the 2x2x2 aggregation hierarchy equals 4^l times
+    the 7-point Laplacian on the (N/2^l)^3 grid (integer-valued)."""
+    L = inputs.laplacian_7pt(N >> level)
+    return L.with_values(L.val * (4.0 ** level))
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_amg_galerkin_closed_form(N):
+    A = inputs.laplacian_7pt(N)
+    level = 0
+    with open(os.path.join(GOLDEN, "amg_galerkin.txt")) as fh:
+        table = {}
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                g, lv, diag, off, nnz_rta, nnz_rtar = map(int, ln.split())
+                table[(g, lv)] = (diag, off, nnz_rta, nnz_rtar)
+    while (N >> level) >= 4:
+        R = inputs.aggregation_2x2x2(N >> level)
+        RtA = oracle.spgemm(oracle.transpose(R), A)
+        Ac = oracle.spgemm(RtA, R)
+        ref = galerkin_closed_form(N, level + 1)
+        assert np.array_equal(Ac.rowptr, ref.rowptr)
+        assert np.array_equal(Ac.col, ref.col)
+        assert np.array_equal(Ac.val, ref.val)
+        diag, off, nnz_rta, nnz_rtar = table[(N >> level, level + 1)]
+        assert RtA.nnz == nnz_rta and Ac.nnz == nnz_rtar
+        assert set(np.unique(Ac.val)) == {float(diag), float(off)}
+        A = inputs.CSR(Ac.nrows, Ac.ncols, Ac.rowptr, Ac.col, Ac.val)
+        level += 1
+
+
+@pytest.mark.parametrize("c", [1, 2, 3, 4, 8, 16])
+def test_merge_of_kslices_equals_unsplit(c):
+    A = inputs.rmat(9)
+    C = oracle.spgemm(A, A)
+    parts = [oracle.spgemm(As, Bs) for As, Bs in oracle.kslice(A, A, c)]
+    # paper bound on the intermediate (Sec. 4.4): nnz(C^int) <= flops
+    assert sum(P.nnz for P in parts) <= oracle.row_flops(A, A).sum()
+    assert sum(P.nnz for P in parts) >= C.nnz
+    S = oracle.sum_partials(parts)
+    assert np.array_equal(S.rowptr, C.rowptr)
+    assert np.array_equal(S.col, C.col)
+    np.testing.assert_allclose(S.val, C.val, rtol=1e-12)
+    if c == 1:
+        assert np.array_equal(S.val, C.val)
+
+
+def test_merge_integer_bitexact_and_empty_slices():
+    A = inputs.random_csr(20, 3, 0.5, 1, value="int")
+    B = inputs.random_csr(3, 25, 0.5, 2, value="int")
+    C = oracle.spgemm(A, B)
+    for c in (1, 3, 5, 7):                               # c > l gives empty slices
+        parts = [oracle.spgemm(As, Bs) for As, Bs in oracle.kslice(A, B, c)]
+        S = oracle.sum_partials(parts)
+        assert np.array_equal(S.col, C.col) and np.array_equal(S.val, C.val)
+
+
+def test_kslice_bounds_cover_inner_dimension():
+    for l, c in itertools.product([0, 1, 5, 16, 17, 262144], [1, 2, 3, 4, 16]):
+        b = oracle.kslice_bounds(l, c)
+        assert b[0][0] == 0 and b[-1][1] == l
+        assert all(b[s][1] == b[s + 1][0] for s in range(c - 1))
+        assert all(hi - lo in (l // c, l // c + 1) for lo, hi in b)
+
+
+def test_mcl_prune_renorm():
+    M = inputs.mcl_transition(8)
+    P = oracle.spgemm(M, M)
+    Q = oracle.mcl_prune_renorm(P, 1e-2)
+    pv = np.asarray(P.val)
+    assert Q.nnz == int((pv >= 1e-2).sum())
+    assert np.all(Q.val > 0)
+    for i in range(0, Q.nrows, 7):
+        a, b = Q.rowptr[i], Q.rowptr[i + 1]
+        sel = pv[P.rowptr[i]:P.rowptr[i + 1]] >= 1e-2
+        assert np.array_equal(Q.col[a:b], np.asarray(P.col[P.rowptr[i]:P.rowptr[i + 1]])[sel])
+        if b > a:
+            assert abs(Q.val[a:b].sum() - 1.0) <= 1e-13
