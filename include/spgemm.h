@@ -1,0 +1,203 @@
+/*
+ * spgemm.h -- C ABI of the GB300 sparse matrix-matrix product library.
+ *
+ * The library computes C = A.B for sparse A (m x l) and B (l x n) in CSR,
+ * row by row (Gustavson's algorithm, Alg. 1 of Azad et al., "Exploiting
+ * Multiple Levels of Parallelism in Sparse Matrix-Matrix Multiplication",
+ * written column-wise there; here on rows, the same method on the transposed
+ * problem), in two phases on the GPU: a symbolic phase that counts the
+ * nonzeros of every row of C, and a numeric phase that fills columns and
+ * values.  A second entry family sums the partial products of k-slices of the
+ * inner dimension (the multiway merge with duplicate reduction of Sec. 4.3,
+ * the LocalMerge step of Alg. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All matrix arrays are DEVICE pointers owned by the caller.  The library
+ *   never frees caller memory and never keeps a pointer after the call that
+ *   consumes it returns, except inside a plan (see spgemm_plan), which keeps
+ *   the A/B descriptors and the plan workspace until spgemm_plan_destroy.
+ * - Row pointers are int64 (nnz(C) can exceed 2^31).  Column indices are
+ *   int32 or int64 (spgemm_csr.index_type); C uses the index type of A.
+ * - Rows must have strictly ascending column indices (no duplicates) and
+ *   0-based indices; C is produced the same way (the paper keeps columns
+ *   sorted, Sec. 5.2).  The pattern is structural: products that sum to zero
+ *   stay in C (explicit zeros are nonzeros, Sec. 5).
+ * - Values: F64, F32 and I64 use the (+, x) semiring (I64 wraps around);
+ *   BOOL is the (or, and) semiring and carries no value array.  Every output
+ *   entry is the sum of its products in ascending k, each product rounded
+ *   before it is added (no fused multiply-add), so F64/F32 results are
+ *   reproducible bit for bit from run to run.
+ * - Work is enqueued on the caller's CUDA stream (a cudaStream_t passed as
+ *   void*; NULL = legacy default stream).  The calls that report a size to
+ *   the host (spgemm_plan, spgemm_symbolic, spgemm_merge_symbolic) wait for
+ *   that stream; the others return without waiting.
+ * - Errors: every call returns a spgemm_status; on error the outputs are
+ *   unspecified and spgemm_last_error() gives a message (thread-local).  No
+ *   exception crosses the ABI.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID_ARG = 1,    /* null pointer, negative size, dimension mismatch */
+    SPGEMM_ERR_INVALID_CSR = 2,    /* checked mode: rowptr not monotone, column out of
+                                      range, unsorted or duplicate columns */
+    SPGEMM_ERR_INDEX_OVERFLOW = 3, /* a column index or nnz does not fit the index type */
+    SPGEMM_ERR_OUT_OF_MEMORY = 4,  /* a caller workspace is smaller than required */
+    SPGEMM_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    SPGEMM_ERR_CUDA = 6,           /* a CUDA runtime call failed (message has the code) */
+    SPGEMM_ERR_NOT_SUPPORTED = 7,  /* a combination this build does not implement */
+    SPGEMM_ERR_INTERNAL = 8        /* a device-side consistency check failed */
+} spgemm_status;
+
+typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_I64 = 2, SPGEMM_BOOL = 3 } spgemm_value_type;
+typedef enum { SPGEMM_INDEX_I32 = 0, SPGEMM_INDEX_I64 = 1 } spgemm_index_type;
+typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_OR_AND = 1 } spgemm_semiring;
+
+/* A CSR matrix in device memory.
+ *   rowptr  int64[nrows+1]; row i spans [rowptr[i], rowptr[i+1]) ...
+ *   rowend  ... or, when non-NULL, [rowptr[i], rowend[i]) (int64[nrows]); this
+ *           lets a k-slice of A be a view on A's own arrays (Alg. 2 splits
+ *           the inner dimension into contiguous ranges, Sec. 4.1).
+ *   col     int32 or int64 [nnz] per index_type
+ *   val     double / float / int64 [nnz] per value_type; NULL for BOOL
+ *   nnz     length of the col/val arrays (the largest row end) */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const int64_t* rowptr;
+    const int64_t* rowend;
+    const void* col;
+    const void* val;
+    int32_t index_type; /* spgemm_index_type */
+    int32_t value_type; /* spgemm_value_type */
+} spgemm_csr;
+
+typedef struct {
+    int32_t semiring;    /* spgemm_semiring; OR_AND ignores values and yields a pattern */
+    int32_t checked;     /* nonzero: validate A and B on the device before planning */
+    int32_t dense_chunk; /* columns per dense-row chunk: 0 = library choice, 1024 or 2048 */
+    int32_t reserved[5]; /* must be zero */
+} spgemm_opts;
+
+typedef struct spgemm_plan_s* spgemm_plan_t;
+
+/* Row statistics gathered by spgemm_plan (flops as defined in Sec. 2: the
+ * number of scalar multiplications, sum over rows of sum_{k in A(i,:)}
+ * nnz(B(k,:))). */
+typedef struct {
+    int64_t m, l, n;
+    int64_t flops;          /* total multiplications */
+    int64_t max_row_flops;
+    int64_t rows_empty;     /* rows with no products */
+    int64_t rows_hash;      /* rows handled with per-warp hash tables */
+    int64_t rows_dense;     /* rows handled with column-chunked dense accumulators */
+    int64_t chunk_width;    /* columns per dense chunk */
+    int64_t chunks_per_row; /* dense chunks per dense row */
+    int64_t nnz_c;          /* set by spgemm_symbolic, -1 before */
+} spgemm_info;
+
+/* Number of kernels this library has launched in this process (all
+ * devices, all threads); a diagnostic counter, never reset. */
+int64_t spgemm_kernel_launches(void);
+
+/* Library version string. */
+const char* spgemm_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* spgemm_last_error(void);
+
+/* Bytes of device workspace spgemm_plan needs for an m-row A (pure function;
+ * O(m)). */
+size_t spgemm_plan_workspace_size(int64_t m);
+
+/* spgemm_plan -- validate A and B, count flops per row and bin the rows by
+ * their flops (the per-row flops of Sec. 2 decide which accumulator a row
+ * gets).  Enqueues the row analysis on `stream`, waits for it, and returns a
+ * plan that owns host state only.  `plan_ws` (>= spgemm_plan_workspace_size
+ * bytes, 256-byte aligned, device memory) must stay alive and untouched until
+ * spgemm_plan_destroy.  A and B arrays must stay alive and unchanged for the
+ * life of the plan.  Errors: INVALID_ARG, INVALID_CSR (checked mode),
+ * INDEX_OVERFLOW, OUT_OF_MEMORY (plan_ws too small), NOT_SUPPORTED, CUDA. */
+spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                          void* stream, void* plan_ws, size_t plan_ws_bytes,
+                          spgemm_plan_t* plan);
+
+/* Statistics of a plan (host call, no device work). */
+spgemm_status spgemm_plan_info(spgemm_plan_t plan, spgemm_info* info);
+
+/* Device workspace (bytes) that spgemm_symbolic / spgemm_numeric need for
+ * this plan (dense-chunk counts and per-entry cursors).  Host call. */
+spgemm_status spgemm_workspace_size(spgemm_plan_t plan, size_t* bytes);
+
+/* spgemm_symbolic -- count the nonzeros of every row of C (the size of the
+ * union of the column sets of the rows of B selected by A(i,:)), write the
+ * row pointers rowptrC (int64[m+1], device) and nnz(C) to *nnz_c (host).
+ * Waits for the stream.  `ws` is the workspace of spgemm_workspace_size; it
+ * must be passed unchanged to spgemm_numeric. */
+spgemm_status spgemm_symbolic(spgemm_plan_t plan, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                              int64_t* nnz_c);
+
+/* spgemm_numeric -- fill colC (index type of A, [nnz_c]) and valC (value
+ * type of A, [nnz_c]; NULL for OR_AND/BOOL) given the rowptrC of
+ * spgemm_symbolic.  C(i,j) = sum over k ascending of A(i,k)*B(k,j) (Alg. 1).
+ * Does not wait for the stream. */
+spgemm_status spgemm_numeric(spgemm_plan_t plan, void* ws, size_t ws_bytes,
+                             const int64_t* rowptrC, void* colC, void* valC);
+
+/* Reads the plan's device error word (waits for the stream).  Returns
+ * SPGEMM_ERR_INTERNAL if a device-side check failed since the plan was
+ * made. */
+spgemm_status spgemm_check(spgemm_plan_t plan);
+
+/* Release a plan (host memory only; the caller frees plan_ws). */
+void spgemm_plan_destroy(spgemm_plan_t plan);
+
+/* ---- k-slices and their merge (Alg. 2 split of the inner dimension;
+ *      multiway merge with duplicate reduction, Sec. 4.3) ---- */
+
+/* spgemm_kslice_bounds -- for A (m x l, CSR, no rowend), write the c+1
+ * boundary arrays bounds[s*m + i] (int64, device, (c+1)*m entries) so that
+ * slice s of row i is [bounds[s*m+i], bounds[(s+1)*m+i]): the entries of
+ * A(i,:) with column in K_s = [floor(s*l/c), floor((s+1)*l/c)).  Slice s of A
+ * is then the view {rowptr = bounds + s*m, rowend = bounds + (s+1)*m} on A's
+ * arrays, and C_s = A_s . B.  Does not wait. */
+spgemm_status spgemm_kslice_bounds(const spgemm_csr* A, int32_t c, void* stream,
+                                   int64_t* bounds);
+
+/* Workspace for the merge of c partials with m rows. */
+size_t spgemm_merge_workspace_size(int32_t c, int64_t m, int64_t n);
+
+/* spgemm_merge_symbolic -- parts[0..c-1]: c partial products of equal shape
+ * (sorted rows).  Writes rowptrC (int64[m+1]) of C = sum_s parts[s] and
+ * nnz(C) (host).  Waits for the stream. */
+spgemm_status spgemm_merge_symbolic(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                    void* stream, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                                    int64_t* nnz_c);
+
+/* spgemm_merge_numeric -- fill colC/valC of C = sum_s parts[s]; equal
+ * (i,j) entries are added in ascending s.  Does not wait. */
+spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                   void* stream, void* ws, size_t ws_bytes,
+                                   const int64_t* rowptrC, void* colC, void* valC);
+
+/* Reads the device error word the merge calls record in `ws` (waits for the
+ * stream); SPGEMM_ERR_INTERNAL if a row's emitted count disagreed with
+ * rowptrC. */
+spgemm_status spgemm_merge_check(void* stream, void* ws);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_GB300_H */

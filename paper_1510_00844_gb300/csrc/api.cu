@@ -1,0 +1,496 @@
+// C ABI of the library (declared in include/spgemm.h): argument checks,
+// plan bookkeeping, dispatch on index/value type, error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "plan.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+spgemm_status fail(spgemm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+spgemm_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(SPGEMM_ERR_CUDA, "%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+}
+
+#define SG_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);   \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_value_type(int32_t v) { return v >= SPGEMM_F64 && v <= SPGEMM_BOOL; }
+bool valid_index_type(int32_t t) { return t == SPGEMM_INDEX_I32 || t == SPGEMM_INDEX_I64; }
+
+spgemm_status check_csr(const spgemm_csr* M, const char* name, bool need_vals) {
+    if (!M) return fail(SPGEMM_ERR_INVALID_ARG, "%s is NULL", name);
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0)
+        return fail(SPGEMM_ERR_INVALID_ARG, "%s has a negative size", name);
+    if (!valid_index_type(M->index_type))
+        return fail(SPGEMM_ERR_INVALID_ARG, "%s.index_type invalid", name);
+    if (!valid_value_type(M->value_type))
+        return fail(SPGEMM_ERR_INVALID_ARG, "%s.value_type invalid", name);
+    if (!M->rowptr) return fail(SPGEMM_ERR_INVALID_ARG, "%s.rowptr is NULL", name);
+    if (M->nnz > 0 && !M->col) return fail(SPGEMM_ERR_INVALID_ARG, "%s.col is NULL", name);
+    if (need_vals && M->nnz > 0 && !M->val)
+        return fail(SPGEMM_ERR_INVALID_ARG, "%s.val is NULL", name);
+    if (M->index_type == SPGEMM_INDEX_I32 && (M->ncols > 0x7fffffffLL || M->nrows > 0x7fffffffLL))
+        return fail(SPGEMM_ERR_INDEX_OVERFLOW, "%s dimensions exceed int32 indices", name);
+    if (M->nrows > 0x7fffffffLL)
+        return fail(SPGEMM_ERR_NOT_SUPPORTED, "%s has more than 2^31-1 rows", name);
+    return SPGEMM_OK;
+}
+
+// value type the kernels use: BOOL for the (or, and) semiring
+int kernel_value_type(const spgemm_csr* A, const spgemm_opts* o) {
+    if ((o && o->semiring == SPGEMM_OR_AND) || A->value_type == SPGEMM_BOOL) return SPGEMM_BOOL;
+    return A->value_type;
+}
+
+int device_sm_count(int* smem_optin) {
+    int dev = 0, sms = 1, optin = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    if (smem_optin) *smem_optin = optin;
+    return sms;
+}
+
+}  // namespace
+
+namespace sg {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+WsLayout workspace_layout(const Plan& P) {
+    WsLayout L;
+    size_t off = 0;
+    L.chunkcnt = off;
+    off += align_up((size_t)P.ndense * (size_t)P.P * sizeof(int32_t));
+    L.segtab = off;
+    if (P.ndense > 0) off += align_up((size_t)P.l * (kSegGrid + 1) * sizeof(int32_t));
+    L.arena = off;
+    L.arena_stride = std::max<long long>(1, P.max_dense_len);
+    if (P.ndense > 0)
+        off += align_up((size_t)P.dense_grid * P.dense_warps_per_block * (size_t)L.arena_stride *
+                        sizeof(longlong2));
+    L.scan = off;
+    off += align_up(scan_temp_bytes(P.m + 1));
+    L.total = off;
+    return L;
+}
+
+// Units of the dense numeric phase: per flops class (floor(log2 flops) = lg),
+// G segments per row with about kSegFlops products per segment.
+void build_dense_units(Plan& P) {
+    constexpr long long kSegFlops = 1LL << 16;
+    DenseUnits& U = P.units;
+    int gmax = 1;
+    while (gmax * 2 <= std::min(kSegGrid, P.P)) gmax *= 2;
+    U.nclass = kMaxDenseClasses;
+    long long rb = 0, ub = 0;
+    for (int t = 0; t < kMaxDenseClasses; ++t) {
+        const int lg = kDenseMaxLog2 - t;
+        long long want = ((lg + 1 >= 62) ? (1LL << 62) : (1LL << (lg + 1))) / kSegFlops;
+        int G = 1;
+        while (G < gmax && G < want) G *= 2;
+        const long long cnt = (long long)P.class_count[kClassDense0 + t];
+        U.G[t] = G;
+        U.row_begin[t] = rb;
+        U.unit_begin[t] = ub;
+        rb += cnt;
+        ub += cnt * G;
+    }
+    U.unit_begin[kMaxDenseClasses] = ub;
+}
+
+}  // namespace sg
+
+extern "C" {
+
+int64_t spgemm_kernel_launches(void) { return sg::g_launches.load(); }
+
+const char* spgemm_version(void) { return "gb300-spgemm 0.1 (sm_103a)"; }
+
+const char* spgemm_last_error(void) { return g_last_error.c_str(); }
+
+size_t spgemm_plan_workspace_size(int64_t m) {
+    if (m < 0) m = 0;
+    return align_up(sizeof(sg::DevCounters)) + align_up((size_t)m * sizeof(int64_t)) +
+           align_up((size_t)m * sizeof(int32_t));
+}
+
+spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                          void* stream, void* plan_ws, size_t plan_ws_bytes,
+                          spgemm_plan_t* plan_out) {
+    g_last_error.clear();
+    if (!plan_out) return fail(SPGEMM_ERR_INVALID_ARG, "plan output pointer is NULL");
+    *plan_out = nullptr;
+    spgemm_opts o{};
+    if (opts) o = *opts;
+    if (o.semiring != SPGEMM_PLUS_TIMES && o.semiring != SPGEMM_OR_AND)
+        return fail(SPGEMM_ERR_INVALID_ARG, "unknown semiring %d", o.semiring);
+    if (o.dense_chunk != 0 && o.dense_chunk != sg::kDenseW0 && o.dense_chunk != sg::kDenseW1)
+        return fail(SPGEMM_ERR_INVALID_ARG, "dense_chunk must be 0, %d or %d", sg::kDenseW0,
+                    sg::kDenseW1);
+    if (!A || !B) return fail(SPGEMM_ERR_INVALID_ARG, "A or B is NULL");
+    const int vt = kernel_value_type(A, &o);
+    const bool need_vals = vt != SPGEMM_BOOL;
+    spgemm_status st;
+    if ((st = check_csr(A, "A", need_vals)) != SPGEMM_OK) return st;
+    if ((st = check_csr(B, "B", need_vals)) != SPGEMM_OK) return st;
+    if (A->ncols != B->nrows)
+        return fail(SPGEMM_ERR_INVALID_ARG, "inner dimensions differ: A is %lld x %lld, B is %lld x %lld",
+                    (long long)A->nrows, (long long)A->ncols, (long long)B->nrows,
+                    (long long)B->ncols);
+    if (A->index_type != B->index_type)
+        return fail(SPGEMM_ERR_INVALID_ARG, "A and B index types differ");
+    if (need_vals && A->value_type != B->value_type)
+        return fail(SPGEMM_ERR_INVALID_ARG, "A and B value types differ");
+    if (B->rowend) return fail(SPGEMM_ERR_INVALID_ARG, "B must be a plain CSR (rowend NULL)");
+    const size_t need = spgemm_plan_workspace_size(A->nrows);
+    if (!plan_ws || plan_ws_bytes < need)
+        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "plan workspace %zu bytes < %zu required",
+                    plan_ws_bytes, need);
+    if (((uintptr_t)plan_ws) % kAlign)
+        return fail(SPGEMM_ERR_INVALID_ARG, "plan workspace not %zu-byte aligned", kAlign);
+
+    Plan* P = new (std::nothrow) Plan();
+    if (!P) return fail(SPGEMM_ERR_OUT_OF_MEMORY, "host allocation of the plan failed");
+    P->A = *A;
+    P->B = *B;
+    P->opts = o;
+    P->stream = (cudaStream_t)stream;
+    P->it = A->index_type;
+    P->vt = vt;
+    P->m = A->nrows;
+    P->l = A->ncols;
+    P->n = B->ncols;
+    P->sm_count = device_sm_count(&P->smem_optin);
+    // the dense symbolic bitmap (n bits) must fit the per-block shared memory
+    P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;
+    P->pws = (unsigned char*)plan_ws;
+    P->pws_bytes = plan_ws_bytes;
+    size_t off = 0;
+    P->cnt = (sg::DevCounters*)(P->pws + off);
+    off += align_up(sizeof(sg::DevCounters));
+    P->flops = (int64_t*)(P->pws + off);
+    off += align_up((size_t)P->m * sizeof(int64_t));
+    P->rows = (int32_t*)(P->pws + off);
+    // dense chunk configuration: wider chunks for 8-byte values on larger n
+    {
+        const size_t vbytes = vt == SPGEMM_F64 || vt == SPGEMM_I64 ? 8 : vt == SPGEMM_F32 ? 4 : 0;
+        int cfg = (vbytes == 8) ? 0 : 1;
+        if (o.dense_chunk == sg::kDenseW0) cfg = 0;
+        if (o.dense_chunk == sg::kDenseW1) cfg = 1;
+        P->W = cfg == 0 ? sg::kDenseW0 : sg::kDenseW1;
+    }
+    P->P = (int)std::max<long long>(1, (P->n + P->W - 1) / P->W);
+
+    auto bail = [&](spgemm_status s) {
+        delete P;
+        return s;
+    };
+    cudaStream_t s = P->stream;
+    cudaError_t e = cudaMemsetAsync(P->cnt, 0, sizeof(sg::DevCounters), s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: memset"));
+    if (o.checked) {
+        int* err = &P->cnt->err;
+        e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(*A, err, P->sm_count, s)
+                                      : sg::launch_validate<int64_t>(*A, err, P->sm_count, s);
+        if (e == cudaSuccess)
+            e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(*B, err, P->sm_count, s)
+                                          : sg::launch_validate<int64_t>(*B, err, P->sm_count, s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: validate"));
+        int herr = 0;
+        e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: validate readback"));
+        if (herr != 0)
+            return bail(fail(SPGEMM_ERR_INVALID_CSR,
+                             "invalid CSR input (%s)",
+                             herr == sg::kDevBadRowptr ? "row pointers not monotone or out of range"
+                                                       : "column index out of range, unsorted or duplicated"));
+    }
+    e = P->it == SPGEMM_INDEX_I32 ? sg::launch_analyze<int32_t>(*P) : sg::launch_analyze<int64_t>(*P);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: analyze"));
+    e = sg::launch_binning(*P);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: binning"));
+    sg::DevCounters h;
+    e = cudaMemcpyAsync(&h, P->cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: readback"));
+    if (h.unsupported)
+        return bail(fail(SPGEMM_ERR_NOT_SUPPORTED,
+                         "rows with more than 1024 products need n <= %lld columns (n = %lld)",
+                         P->max_dense_n, P->n));
+    long long acc = 0;
+    for (int c = 0; c < sg::kNumClasses; ++c) {
+        P->class_count[c] = h.class_count[c];
+        P->class_off[c] = acc;
+        acc += (long long)h.class_count[c];
+    }
+    P->class_off[sg::kNumClasses] = acc;
+    P->total_flops = (long long)h.total_flops;
+    P->max_flops = (long long)h.max_flops;
+    P->ndense = acc - P->class_off[sg::kClassDense0];
+    P->max_dense_len = (long long)h.max_dense_len;
+    sg::build_dense_units(*P);
+    {
+        const bool i32 = P->it == SPGEMM_INDEX_I32;
+        switch (P->vt) {
+            case SPGEMM_F64:
+                e = i32 ? sg::prepare_numeric<int32_t, double>(*P) : sg::prepare_numeric<int64_t, double>(*P);
+                break;
+            case SPGEMM_F32:
+                e = i32 ? sg::prepare_numeric<int32_t, float>(*P) : sg::prepare_numeric<int64_t, float>(*P);
+                break;
+            case SPGEMM_I64:
+                e = i32 ? sg::prepare_numeric<int32_t, int64_t>(*P) : sg::prepare_numeric<int64_t, int64_t>(*P);
+                break;
+            default:
+                e = i32 ? sg::prepare_numeric<int32_t, sg::NoVal>(*P) : sg::prepare_numeric<int64_t, sg::NoVal>(*P);
+                break;
+        }
+        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: numeric setup"));
+    }
+    *plan_out = P;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_info(spgemm_plan_t P, spgemm_info* info) {
+    if (!P || !info) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    info->m = P->m;
+    info->l = P->l;
+    info->n = P->n;
+    info->flops = P->total_flops;
+    info->max_row_flops = P->max_flops;
+    info->rows_empty = (int64_t)P->class_count[sg::kClassEmpty];
+    long long h = 0;
+    for (int b = 0; b < sg::kNumHashBins; ++b) h += (long long)P->class_count[sg::kClassHash0 + b];
+    info->rows_hash = h;
+    info->rows_dense = P->ndense;
+    info->chunk_width = P->W;
+    info->chunks_per_row = P->P;
+    info->nnz_c = P->nnz_c;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_workspace_size(spgemm_plan_t P, size_t* bytes) {
+    if (!P || !bytes) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    *bytes = sg::workspace_layout(*P).total;
+    return SPGEMM_OK;
+}
+
+static spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes) {
+    size_t need = sg::workspace_layout(*P).total;
+    if (need > 0 && (!ws || ws_bytes < need))
+        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "workspace %zu bytes < %zu required", ws_bytes, need);
+    if (ws && ((uintptr_t)ws) % kAlign)
+        return fail(SPGEMM_ERR_INVALID_ARG, "workspace not %zu-byte aligned", kAlign);
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_symbolic(spgemm_plan_t P, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                              int64_t* nnz_c) {
+    g_last_error.clear();
+    if (!P || !rowptrC || !nnz_c) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    spgemm_status st = check_ws(P, ws, ws_bytes);
+    if (st != SPGEMM_OK) return st;
+    cudaStream_t s = P->stream;
+    unsigned char* w = (unsigned char*)ws;
+    SG_CUDA(cudaMemsetAsync(rowptrC + P->m, 0, sizeof(int64_t), s), "symbolic: memset");
+    cudaError_t e = P->it == SPGEMM_INDEX_I32 ? sg::launch_symbolic<int32_t>(*P, w, rowptrC)
+                                              : sg::launch_symbolic<int64_t>(*P, w, rowptrC);
+    if (e != cudaSuccess) return cuda_fail(e, "symbolic");
+    sg::WsLayout L = sg::workspace_layout(*P);
+    e = sg::launch_exclusive_scan(rowptrC, P->m + 1, (int64_t*)(w + L.scan), s);
+    if (e != cudaSuccess) return cuda_fail(e, "symbolic: scan");
+    int64_t total = 0;
+    int herr = 0;
+    SG_CUDA(cudaMemcpyAsync(&total, rowptrC + P->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+            "symbolic: readback");
+    SG_CUDA(cudaMemcpyAsync(&herr, &P->cnt->err, sizeof(int), cudaMemcpyDeviceToHost, s),
+            "symbolic: readback");
+    SG_CUDA(cudaStreamSynchronize(s), "symbolic: sync");
+    if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed in symbolic phase (code %d)", herr);
+    P->nnz_c = total;
+    *nnz_c = total;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_numeric(spgemm_plan_t P, void* ws, size_t ws_bytes, const int64_t* rowptrC,
+                             void* colC, void* valC) {
+    g_last_error.clear();
+    if (!P || !rowptrC) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    if (P->nnz_c < 0) return fail(SPGEMM_ERR_INVALID_ARG, "spgemm_symbolic has not run on this plan");
+    if (P->nnz_c > 0 && !colC) return fail(SPGEMM_ERR_INVALID_ARG, "colC is NULL");
+    if (P->nnz_c > 0 && P->vt != SPGEMM_BOOL && !valC)
+        return fail(SPGEMM_ERR_INVALID_ARG, "valC is NULL");
+    spgemm_status st = check_ws(P, ws, ws_bytes);
+    if (st != SPGEMM_OK) return st;
+    unsigned char* w = (unsigned char*)ws;
+    cudaError_t e = cudaSuccess;
+    const bool i32 = P->it == SPGEMM_INDEX_I32;
+    switch (P->vt) {
+        case SPGEMM_F64:
+            e = i32 ? sg::launch_numeric<int32_t, double>(*P, w, rowptrC, colC, valC)
+                    : sg::launch_numeric<int64_t, double>(*P, w, rowptrC, colC, valC);
+            break;
+        case SPGEMM_F32:
+            e = i32 ? sg::launch_numeric<int32_t, float>(*P, w, rowptrC, colC, valC)
+                    : sg::launch_numeric<int64_t, float>(*P, w, rowptrC, colC, valC);
+            break;
+        case SPGEMM_I64:
+            e = i32 ? sg::launch_numeric<int32_t, int64_t>(*P, w, rowptrC, colC, valC)
+                    : sg::launch_numeric<int64_t, int64_t>(*P, w, rowptrC, colC, valC);
+            break;
+        default:
+            e = i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, w, rowptrC, colC, nullptr)
+                    : sg::launch_numeric<int64_t, sg::NoVal>(*P, w, rowptrC, colC, nullptr);
+            break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "numeric");
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_check(spgemm_plan_t P) {
+    if (!P) return fail(SPGEMM_ERR_INVALID_ARG, "NULL plan");
+    int herr = 0;
+    SG_CUDA(cudaMemcpyAsync(&herr, &P->cnt->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream),
+            "check: readback");
+    SG_CUDA(cudaStreamSynchronize(P->stream), "check: sync");
+    if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed (code %d)", herr);
+    return SPGEMM_OK;
+}
+
+void spgemm_plan_destroy(spgemm_plan_t P) { delete P; }
+
+spgemm_status spgemm_kslice_bounds(const spgemm_csr* A, int32_t c, void* stream, int64_t* bounds) {
+    g_last_error.clear();
+    spgemm_status st = check_csr(A, "A", false);
+    if (st != SPGEMM_OK) return st;
+    if (c < 1) return fail(SPGEMM_ERR_INVALID_ARG, "slice count must be >= 1");
+    if (A->rowend) return fail(SPGEMM_ERR_INVALID_ARG, "A must be a plain CSR (rowend NULL)");
+    if (!bounds && A->nrows > 0) return fail(SPGEMM_ERR_INVALID_ARG, "bounds is NULL");
+    int sms = device_sm_count(nullptr);
+    cudaError_t e = A->index_type == SPGEMM_INDEX_I32
+                        ? sg::launch_kslice_bounds<int32_t>(*A, c, bounds, sms, (cudaStream_t)stream)
+                        : sg::launch_kslice_bounds<int64_t>(*A, c, bounds, sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kslice_bounds");
+    return SPGEMM_OK;
+}
+
+size_t spgemm_merge_workspace_size(int32_t c, int64_t m, int64_t n) {
+    (void)c;
+    (void)n;
+    if (m < 0) m = 0;
+    return align_up(sizeof(sg::DevCounters)) + align_up(sg::scan_temp_bytes(m + 1));
+}
+
+static spgemm_status check_parts(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                 int* vt_out) {
+    if (c < 1 || c > 32) return fail(SPGEMM_ERR_INVALID_ARG, "merge needs 1 <= c <= 32 parts (c = %d)", c);
+    if (!parts) return fail(SPGEMM_ERR_INVALID_ARG, "parts is NULL");
+    spgemm_opts o{};
+    if (opts) o = *opts;
+    const int vt = kernel_value_type(&parts[0], &o);
+    for (int s = 0; s < c; ++s) {
+        spgemm_status st = check_csr(&parts[s], "part", vt != SPGEMM_BOOL);
+        if (st != SPGEMM_OK) return st;
+        if (parts[s].nrows != parts[0].nrows || parts[s].ncols != parts[0].ncols)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d shape differs from part 0", s);
+        if (parts[s].index_type != parts[0].index_type)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d index type differs", s);
+        if (vt != SPGEMM_BOOL && parts[s].value_type != parts[0].value_type)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d value type differs", s);
+    }
+    *vt_out = vt;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_merge_symbolic(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                    void* stream, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                                    int64_t* nnz_c) {
+    g_last_error.clear();
+    int vt = 0;
+    spgemm_status st = check_parts(c, parts, opts, &vt);
+    if (st != SPGEMM_OK) return st;
+    if (!rowptrC || !nnz_c) return fail(SPGEMM_ERR_INVALID_ARG, "NULL output");
+    const long long m = parts[0].nrows, n = parts[0].ncols;
+    const size_t need = spgemm_merge_workspace_size(c, m, n);
+    if (!ws || ws_bytes < need)
+        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "merge workspace %zu bytes < %zu required", ws_bytes, need);
+    if (((uintptr_t)ws) % kAlign) return fail(SPGEMM_ERR_INVALID_ARG, "workspace not aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* w = (unsigned char*)ws;
+    sg::DevCounters* cnt = (sg::DevCounters*)w;
+    int64_t* temp = (int64_t*)(w + align_up(sizeof(sg::DevCounters)));
+    int sms = device_sm_count(nullptr);
+    SG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(sg::DevCounters), s), "merge: memset");
+    SG_CUDA(cudaMemsetAsync(rowptrC + m, 0, sizeof(int64_t), s), "merge: memset");
+    cudaError_t e = sg::launch_merge(c, parts, vt, m, n, sms, s, false, rowptrC, nullptr, nullptr,
+                                     nullptr, &cnt->err);
+    if (e != cudaSuccess) return cuda_fail(e, "merge symbolic");
+    e = sg::launch_exclusive_scan(rowptrC, m + 1, temp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "merge symbolic: scan");
+    int64_t total = 0;
+    SG_CUDA(cudaMemcpyAsync(&total, rowptrC + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+            "merge: readback");
+    SG_CUDA(cudaStreamSynchronize(s), "merge: sync");
+    *nnz_c = total;
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                   void* stream, void* ws, size_t ws_bytes,
+                                   const int64_t* rowptrC, void* colC, void* valC) {
+    g_last_error.clear();
+    int vt = 0;
+    spgemm_status st = check_parts(c, parts, opts, &vt);
+    if (st != SPGEMM_OK) return st;
+    if (!rowptrC) return fail(SPGEMM_ERR_INVALID_ARG, "rowptrC is NULL");
+    const long long m = parts[0].nrows, n = parts[0].ncols;
+    const size_t need = spgemm_merge_workspace_size(c, m, n);
+    if (!ws || ws_bytes < need)
+        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "merge workspace %zu bytes < %zu required", ws_bytes, need);
+    if (((uintptr_t)ws) % kAlign) return fail(SPGEMM_ERR_INVALID_ARG, "workspace not aligned");
+    if (!colC && m > 0) return fail(SPGEMM_ERR_INVALID_ARG, "colC is NULL");
+    if (vt != SPGEMM_BOOL && !valC && m > 0) return fail(SPGEMM_ERR_INVALID_ARG, "valC is NULL");
+    sg::DevCounters* cnt = (sg::DevCounters*)ws;
+    int sms = device_sm_count(nullptr);
+    cudaError_t e = sg::launch_merge(c, parts, vt, m, n, sms, (cudaStream_t)stream, true, nullptr,
+                                     rowptrC, colC, valC, &cnt->err);
+    if (e != cudaSuccess) return cuda_fail(e, "merge numeric");
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_merge_check(void* stream, void* ws) {
+    if (!ws) return fail(SPGEMM_ERR_INVALID_ARG, "workspace is NULL");
+    int herr = 0;
+    SG_CUDA(cudaMemcpyAsync(&herr, &((sg::DevCounters*)ws)->err, sizeof(int), cudaMemcpyDeviceToHost,
+                            (cudaStream_t)stream), "merge check");
+    SG_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "merge check");
+    if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed in merge (code %d)", herr);
+    return SPGEMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Non-template kernels: row binning, int64 exclusive scan, empty rows; and
+// their host launchers.
+#include "plan.h"
+
+namespace sg {
+
+// Class offsets (exclusive scan of the counts), one thread.
+__global__ void class_offsets_kernel(DevCounters* cnt) {
+    unsigned long long s = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        cnt->class_cursor[c] = s;
+        s += cnt->class_count[c];
+    }
+}
+
+// Scatter row ids into their class segment (order inside a class is free;
+// rows are independent).
+__global__ void bin_rows_kernel(long long m, long long n, long long max_dense_n,
+                                const int64_t* __restrict__ flops, int32_t* __restrict__ rows,
+                                DevCounters* cnt) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c = row_class(flops[i], n, max_dense_n, nullptr);
+        unsigned long long pos = atomicAdd(&cnt->class_cursor[c], 1ull);
+        rows[pos] = (int32_t)i;
+    }
+}
+
+// ------------------------------------------------------------------ scan
+// In-place exclusive scan of int64 x[0..N).  Tiles of 4096 (256 x 16).
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void scan_reduce_kernel(const int64_t* __restrict__ x, long long N,
+                                   int64_t* __restrict__ part) {
+    __shared__ long long ws[kScanThreads / 32];
+    long long base = (long long)blockIdx.x * kScanTile;
+    long long s = 0;
+    for (int t = 0; t < kScanItems; ++t) {
+        long long idx = base + (long long)t * kScanThreads + threadIdx.x;
+        if (idx < N) s += x[idx];
+    }
+    s = warp_sum(s);
+    if (lane_id() == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long v = threadIdx.x < kScanThreads / 32 ? ws[threadIdx.x] : 0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+// Exclusive scan of the tile sums with one block of 1024 threads (carry loop).
+__global__ void scan_partials_kernel(int64_t* part, long long nparts) {
+    __shared__ long long ws[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < nparts; b += blockDim.x) {
+        long long idx = b + threadIdx.x;
+        long long v = idx < nparts ? part[idx] : 0;
+        long long inc = warp_incl_scan(v);
+        if (lane_id() == 31) ws[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            long long w = ws[threadIdx.x];
+            long long wi = warp_incl_scan(w);
+            ws[threadIdx.x] = wi - w;
+        }
+        __syncthreads();
+        long long excl = carry + ws[threadIdx.x >> 5] + inc - v;
+        if (idx < nparts) part[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_apply_kernel(int64_t* __restrict__ x, long long N,
+                                  const int64_t* __restrict__ part) {
+    __shared__ long long ws[kScanThreads / 32];
+    __shared__ long long carry;
+    long long base = (long long)blockIdx.x * kScanTile;
+    if (threadIdx.x == 0) carry = part[blockIdx.x];
+    __syncthreads();
+    for (int t = 0; t < kScanItems; ++t) {
+        long long idx = base + (long long)t * kScanThreads + threadIdx.x;
+        long long v = idx < N ? x[idx] : 0;
+        long long inc = warp_incl_scan(v);
+        if (lane_id() == 31) ws[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            long long w = threadIdx.x < kScanThreads / 32 ? ws[threadIdx.x] : 0;
+            long long wi = warp_incl_scan(w);
+            if (threadIdx.x < kScanThreads / 32) ws[threadIdx.x] = wi - w;
+        }
+        __syncthreads();
+        long long excl = carry + ws[threadIdx.x >> 5] + inc - v;
+        if (idx < N) x[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry = excl + v;
+        __syncthreads();
+    }
+}
+
+// Empty rows: count 0.
+__global__ void zero_rows_kernel(const int32_t* __restrict__ rows, long long nrows,
+                                 int64_t* __restrict__ rowcnt) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+         r += (long long)gridDim.x * blockDim.x)
+        rowcnt[rows[r]] = 0;
+}
+
+
+cudaError_t launch_binning(Plan& P) {
+    const long long m = P.m;
+    count_launches(1);
+    class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt);
+    if (m > 0) {
+        int blocks = (int)std::min<long long>((m + 255) / 256, (long long)P.sm_count * 8);
+        count_launches(1);
+        bin_rows_kernel<<<blocks, 256, 0, P.stream>>>(m, P.n, P.max_dense_n, P.flops, P.rows, P.cnt);
+    }
+    return cudaGetLastError();
+}
+
+size_t scan_temp_bytes(long long N) {
+    long long parts = (N + kScanTile - 1) / kScanTile;
+    return (size_t)std::max<long long>(parts, 1) * sizeof(int64_t);
+}
+
+cudaError_t launch_exclusive_scan(int64_t* x, long long N, int64_t* temp, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    long long parts = (N + kScanTile - 1) / kScanTile;
+    count_launches(1);
+    scan_reduce_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(x, N, temp);
+    count_launches(1);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(temp, parts);
+    count_launches(1);
+    scan_apply_kernel<<<(unsigned)parts, kScanThreads, 0, s>>>(x, N, temp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_rows(const int32_t* rows, long long nrows, int64_t* rowcnt, int sm_count,
+                             cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    int blocks = (int)std::min<long long>((nrows + 255) / 256, (long long)sm_count * 8);
+    count_launches(1);
+    zero_rows_kernel<<<blocks, 256, 0, s>>>(rows, nrows, rowcnt);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

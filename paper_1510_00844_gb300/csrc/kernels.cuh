@@ -1,0 +1,641 @@
+// Kernels of the two-phase sparse product C = A.B (Gustavson, Alg. 1, on
+// CSR rows) and of the k-slice merge (Sec. 4.3).  Templates over the column
+// index type IT (int32_t / int64_t) and the value type V (double, float,
+// int64_t, NoVal for the Boolean semiring).
+//
+// Row classes (decided from flops_i = sum_{k in A(i,:)} nnz(B(k,:)), Sec. 2):
+//   EMPTY       flops_i == 0
+//   HASH(b)     flops_i <= 1024: one warp per row, warp-private hash table in
+//               shared memory (keys for the symbolic phase, keys + values for
+//               the numeric phase), output sorted by a warp bitonic sort.
+//   DENSE(b)    flops_i > 1024: symbolic = one block per row with a bitmap of
+//               all n columns in shared memory (also yields per-chunk counts);
+//               numeric = one warp per row sweeping column chunks of width W
+//               with a dense accumulator, so the output comes out sorted.
+//               DENSE rows are bucketed by floor(log2 flops_i), largest first.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace sg {
+
+constexpr int kNumHashBins = 4;
+__host__ __device__ constexpr int hash_bin_flops(int b) {
+    return b == 0 ? 32 : b == 1 ? 128 : b == 2 ? 512 : 1024;
+}
+constexpr int kDenseMinLog2 = 10;  // flops > 1024 -> dense
+constexpr int kDenseMaxLog2 = 40;
+constexpr int kClassEmpty = 0;
+constexpr int kClassHash0 = 1;
+constexpr int kClassDense0 = kClassHash0 + kNumHashBins;          // largest-flops bucket
+constexpr int kNumClasses = kClassDense0 + (kDenseMaxLog2 - kDenseMinLog2 + 1);
+
+struct DevCounters {
+    unsigned long long class_count[kNumClasses];
+    unsigned long long class_cursor[kNumClasses];
+    unsigned long long total_flops;
+    unsigned long long max_flops;
+    unsigned long long work_counter[4];  // dynamic row grabbing
+    unsigned long long max_dense_len;    // longest A row among dense rows
+    int err;
+    int unsupported;
+    int pad[30];
+};
+
+__host__ __device__ __forceinline__ int row_class(long long flops, long long n, long long max_dense_n,
+                                                   int* unsupported) {
+    if (flops == 0) return kClassEmpty;
+#pragma unroll
+    for (int b = 0; b < kNumHashBins; ++b)
+        if (flops <= hash_bin_flops(b)) return kClassHash0 + b;
+    if (n > max_dense_n && unsupported) *unsupported = 1;
+#ifdef __CUDA_ARCH__
+    int lg = 63 - __clzll(flops);
+#else
+    int lg = 63 - __builtin_clzll((unsigned long long)flops);
+#endif
+    if (lg > kDenseMaxLog2) lg = kDenseMaxLog2;
+    return kClassDense0 + (kDenseMaxLog2 - lg);
+}
+
+__device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* re, long long i) {
+    return re ? re[i] : rp[i + 1];
+}
+
+// ----------------------------------------------------------------- K1: flops
+// One warp per row: flops_i, its class, per-class counts, total and max.
+template <class IT>
+__global__ void analyze_kernel(long long m, long long n, long long max_dense_n,
+                               const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
+                               const IT* __restrict__ ciA, const int64_t* __restrict__ rpB,
+                               int64_t* __restrict__ flops_out, DevCounters* cnt) {
+    __shared__ unsigned long long hist[kNumClasses];
+    __shared__ unsigned long long blk_total, blk_max, blk_dlen;
+    __shared__ int blk_unsup;
+    for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) hist[t] = 0;
+    if (threadIdx.x == 0) {
+        blk_total = 0;
+        blk_max = 0;
+        blk_dlen = 0;
+        blk_unsup = 0;
+    }
+    __syncthreads();
+    const int lane = lane_id();
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_total = 0, my_max = 0;
+    for (long long i = warp; i < m; i += nwarps) {
+        long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        long long f = 0;
+        for (long long p = a0 + lane; p < a1; p += 32) {
+            long long k = (long long)ciA[p];
+            f += rpB[k + 1] - rpB[k];
+        }
+        f = warp_sum(f);
+        if (lane == 0) {
+            flops_out[i] = f;
+            int uns = 0;
+            int c = row_class(f, n, max_dense_n, &uns);
+            if (uns) blk_unsup = 1;
+            atomicAdd(&hist[c], 1ull);
+            if (c >= kClassDense0) atomicMax(&blk_dlen, (unsigned long long)(a1 - a0));
+            my_total += (unsigned long long)f;
+            if ((unsigned long long)f > my_max) my_max = (unsigned long long)f;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&blk_total, my_total);
+        atomicMax(&blk_max, my_max);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x)
+        if (hist[t]) atomicAdd(&cnt->class_count[t], hist[t]);
+    if (threadIdx.x == 0) {
+        atomicAdd(&cnt->total_flops, blk_total);
+        atomicMax(&cnt->max_flops, blk_max);
+        atomicMax(&cnt->max_dense_len, blk_dlen);
+        if (blk_unsup) atomicExch(&cnt->unsupported, 1);
+    }
+}
+
+// ----------------------------------------------------------- checked mode
+// One warp per row: rowptr monotone, columns in [0, ncols), strictly ascending.
+template <class IT>
+__global__ void validate_kernel(long long m, long long ncols, long long nnz, const int64_t* rp,
+                                const int64_t* re, const IT* ci, int* err) {
+    const int lane = lane_id();
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < m; i += nwarps) {
+        long long a0 = rp[i], a1 = row_end(rp, re, i);
+        if (a0 < 0 || a1 < a0 || a1 > nnz || (!re && i == 0 && a0 != 0)) {
+            if (lane == 0) atomicExch(err, (int)kDevBadRowptr);
+            continue;
+        }
+        for (long long p = a0 + lane; p < a1; p += 32) {
+            long long c = (long long)ci[p];
+            bool bad = c < 0 || c >= ncols || (p + 1 < a1 && (long long)ci[p + 1] <= c);
+            if (bad) atomicExch(err, (int)kDevBadIndex);
+        }
+    }
+}
+
+// --------------------------------------------------- symbolic: hash rows
+// One warp per row; table of 2^LOG2T keys per warp.  Row count -> rowcnt[i].
+template <class IT, int LOG2T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    symbolic_hash_kernel(const int32_t* __restrict__ rows, long long nrows,
+                         const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
+                         const IT* __restrict__ ciA, const int64_t* __restrict__ rpB,
+                         const IT* __restrict__ ciB, int64_t* __restrict__ rowcnt, int* err) {
+    using K = typename KeyT<IT>::type;
+    constexpr int T = 1 << LOG2T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    K* keys = reinterpret_cast<K*>(smem_raw) + (size_t)w * T;
+    for (int s = lane; s < T; s += 32) keys[s] = K(-1);
+    __syncwarp();
+    const long long gw = (long long)blockIdx.x * WARPS + w;
+    const long long nw = (long long)gridDim.x * WARPS;
+    for (long long r = gw; r < nrows; r += nw) {
+        const long long i = rows[r];
+        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        int count = 0;
+        for (long long b = a0; b < a1; b += 32) {
+            const int nb = (int)min(32LL, a1 - b);
+            long long lo = 0;
+            int len = 0;
+            if (lane < nb) {
+                long long k = (long long)ciA[b + lane];
+                lo = rpB[k];
+                len = (int)(rpB[k + 1] - lo);
+            }
+            walk_flat4(nb, lo, len, [&](const long long (&q)[4], const int (&)[4],
+                                        const bool (&valid)[4]) {
+                K kk[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) kk[t] = valid[t] ? (K)ciB[q[t]] : K(-1);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    bool is_new = false;
+                    if (valid[t]) hash_insert<LOG2T>(keys, kk[t], is_new, err);
+                    count += __popc(__ballot_sync(kFull, is_new));
+                }
+            });
+        }
+        if (lane == 0) rowcnt[i] = count;
+        for (int s = lane; s < T; s += 32) keys[s] = K(-1);
+        __syncwarp();
+    }
+}
+
+// -------------------------------------------------- symbolic: dense rows
+// One block per row (dynamic row grabbing), bitmap of all n columns in shared
+// memory.  Also writes the per-chunk counts chunkcnt[r*P + c] (chunk c covers
+// columns [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
+template <class IT>
+__global__ void symbolic_dense_kernel(const int32_t* __restrict__ rows, long long nrows,
+                                      const int64_t* __restrict__ rpA,
+                                      const int64_t* __restrict__ reA, const IT* __restrict__ ciA,
+                                      const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
+                                      long long n, int chunk_words, int P,
+                                      int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
+                                      unsigned long long* work) {
+    extern __shared__ unsigned bm[];
+    __shared__ long long row_total;
+    __shared__ long long cur_row;
+    const int NW = (int)((n + 31) >> 5);
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < NW; t += blockDim.x) bm[t] = 0u;
+    if (threadIdx.x == 0) row_total = 0;
+    __syncthreads();
+    while (true) {
+        if (threadIdx.x == 0) cur_row = (long long)atomicAdd(work, 1ull);
+        __syncthreads();
+        const long long r = cur_row;
+        if (r >= nrows) break;
+        const long long i = rows[r];
+        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        for (long long b = a0 + (long long)w * 32; b < a1; b += (long long)nwarps * 32) {
+            const int nb = (int)min(32LL, a1 - b);
+            long long lo = 0;
+            int len = 0;
+            if (lane < nb) {
+                long long k = (long long)ciA[b + lane];
+                lo = rpB[k];
+                len = (int)(rpB[k + 1] - lo);
+            }
+            walk_batch4(nb, lo, len, [&](const long long (&q)[4], const int (&)[4],
+                                         const bool (&valid)[4], bool) {
+                long long j[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) j[t] = valid[t] ? (long long)ciB[q[t]] : -1;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (j[t] >= 0) atomicOr(&bm[j[t] >> 5], 1u << (j[t] & 31));
+            });
+        }
+        __syncthreads();
+        long long part = 0;
+        for (int c = w; c < P; c += nwarps) {
+            const int w0 = c * chunk_words;
+            const int w1 = min(NW, w0 + chunk_words);
+            int s = 0;
+            for (int t = w0 + lane; t < w1; t += 32) {
+                s += __popc(bm[t]);
+                bm[t] = 0u;
+            }
+            s = warp_sum(s);
+            if (lane == 0) chunkcnt[r * P + c] = s;
+            part += s;
+        }
+        if (lane == 0 && part) atomicAdd((unsigned long long*)&row_total, (unsigned long long)part);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            rowcnt[i] = row_total;
+            row_total = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------- numeric: hash rows
+template <class K, class V>
+__device__ __forceinline__ void warp_bitonic_sort(K* keys, V* vals, int N) {
+    const int lane = lane_id();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < N; i += 32) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    K ki = keys[i], kj = keys[ixj];
+                    bool up = (i & k) == 0;
+                    if ((ki > kj) == up) {
+                        keys[i] = kj;
+                        keys[ixj] = ki;
+                        if constexpr (VOps<V>::has_val) {
+                            V t = vals[i];
+                            vals[i] = vals[ixj];
+                            vals[ixj] = t;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// One warp per row; table of 2^LOG2T (key, value) slots; products added in
+// ascending k (ordered rounds); table compacted, sorted, written.
+template <class IT, class V, int LOG2T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    numeric_hash_kernel(const int32_t* __restrict__ rows, long long nrows,
+                        const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
+                        const IT* __restrict__ ciA, const V* __restrict__ vA,
+                        const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
+                        const V* __restrict__ vB, const int64_t* __restrict__ rpC,
+                        IT* __restrict__ ciC, V* __restrict__ vC, int* err) {
+    using K = typename KeyT<IT>::type;
+    constexpr int T = 1 << LOG2T;
+    constexpr bool HV = VOps<V>::has_val;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    // layout per warp: T values (if any) then T keys
+    constexpr size_t vbytes = HV ? sizeof(V) * T : 0;
+    unsigned char* base = smem_raw + (size_t)w * (vbytes + sizeof(K) * T);
+    V* acc = reinterpret_cast<V*>(base);
+    K* keys = reinterpret_cast<K*>(base + vbytes);
+    for (int s = lane; s < T; s += 32) {
+        keys[s] = K(-1);
+        if constexpr (HV) acc[s] = VOps<V>::init();
+    }
+    __syncwarp();
+    const long long gw = (long long)blockIdx.x * WARPS + w;
+    const long long nw = (long long)gridDim.x * WARPS;
+    for (long long r = gw; r < nrows; r += nw) {
+        const long long i = rows[r];
+        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        for (long long b = a0; b < a1; b += 32) {
+            const int nb = (int)min(32LL, a1 - b);
+            long long lo = 0;
+            int len = 0;
+            V a = VOps<V>::init();
+            if (lane < nb) {
+                long long k = (long long)ciA[b + lane];
+                lo = rpB[k];
+                len = (int)(rpB[k + 1] - lo);
+                a = load_val(vA, b + lane);
+            }
+            walk_batch(nb, lo, len, [&](long long q, int e, bool valid, bool ordered) {
+                V ae = shfl_val(a, e);
+                int slot = -1;
+                V v{};
+                if (valid) {
+                    bool is_new;
+                    slot = hash_insert<LOG2T>(keys, (K)ciB[q], is_new, err);
+                    v = VOps<V>::mul(ae, load_val(vB, q));
+                }
+                valid = valid && slot >= 0;
+                if (ordered) ordered_add(acc, slot, valid, v);
+                else plain_add(acc, slot, valid, v);
+            });
+        }
+        // compact occupied slots to the front (ascending slot order)
+        const long long out = rpC[i];
+        const int cnt = (int)(rpC[i + 1] - out);
+        int pos = 0;
+        for (int s0 = 0; s0 < T; s0 += 32) {
+            K kk = keys[s0 + lane];
+            V vv{};
+            if constexpr (HV) vv = acc[s0 + lane];
+            bool occ = kk != K(-1);
+            unsigned msk = __ballot_sync(kFull, occ);
+            __syncwarp();
+            int p = pos + __popc(msk & lanemask_lt());
+            if (occ) {
+                keys[p] = kk;
+                if constexpr (HV) acc[p] = vv;
+            }
+            pos += __popc(msk);
+            __syncwarp();
+        }
+        if (pos != cnt && lane == 0) atomicExch(err, (int)kDevCountMismatch);
+        int N = 1;
+        while (N < pos) N <<= 1;
+        const K kmax = sizeof(K) == 4 ? (K)0x7fffffff : (K)0x7fffffffffffffffLL;
+        for (int s = pos + lane; s < N; s += 32) keys[s] = kmax;
+        __syncwarp();
+        warp_bitonic_sort<K, V>(keys, acc, N);
+        const int lim = min(pos, cnt);
+        for (int t = lane; t < lim; t += 32) {
+            ciC[out + t] = (IT)keys[t];
+            if constexpr (HV) vC[out + t] = acc[t];
+        }
+        __syncwarp();
+        for (int s = lane; s < T; s += 32) {
+            keys[s] = K(-1);
+            if constexpr (HV) acc[s] = VOps<V>::init();
+        }
+        __syncwarp();
+    }
+}
+
+// --------------------------------------------------- numeric: dense rows
+// Work units: a dense row's P column chunks (width W) are cut into G equal
+// segments (G in {1, 2, 4, ..., kSegGrid}, chosen per flops class so that a
+// unit carries a bounded share of flops); one warp owns a unit.  For each
+// chunk of its segment the warp walks A(i,:) in order and, per entry, the part
+// of B(k,:) inside the chunk, found from a cursor that the previous chunk left
+// (the first cursor of a segment comes from segtab, the position of the first
+// column >= the segment start in every B row).  Products go into a dense
+// accumulator acc[W] with presence flags, in ascending k; the chunk is then
+// emitted in column order.  Cursors live in a per-warp arena slot.
+constexpr int kSegGrid = 16;
+// Dense chunk configurations (columns per chunk, warps per block): one is
+// chosen per plan (spgemm_opts.reserved[0] = 1 or 2 forces one).
+constexpr int kDenseW0 = 1024, kDenseWarps0 = 8;
+constexpr int kDenseW1 = 2048, kDenseWarps1 = 4;
+constexpr int kMaxDenseClasses = kNumClasses - kClassDense0;
+
+struct DenseUnits {
+    int nclass;
+    int G[kMaxDenseClasses];
+    long long row_begin[kMaxDenseClasses];
+    long long unit_begin[kMaxDenseClasses + 1];
+};
+
+__host__ __device__ __forceinline__ long long seg_chunk(int g, int P) {
+    return ((long long)g * P) / kSegGrid;
+}
+
+// segtab[k * (kSegGrid+1) + g] = first position p in B(k,:) with col >= seg_chunk(g)*W,
+// relative to rowptr[k].
+template <class IT>
+__global__ void segtab_kernel(long long l, const int64_t* __restrict__ rpB,
+                              const IT* __restrict__ ciB, int W, int P,
+                              int32_t* __restrict__ segtab) {
+    const long long total = l * (kSegGrid + 1);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long k = t / (kSegGrid + 1);
+        const int g = (int)(t - k * (kSegGrid + 1));
+        const long long key = seg_chunk(g, P) * W;
+        long long lo = rpB[k], hi = rpB[k + 1];
+        const long long base = lo;
+        while (lo < hi) {
+            long long mid = (lo + hi) >> 1;
+            if ((long long)ciB[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        segtab[t] = (int32_t)(lo - base);
+    }
+}
+
+template <class IT, class V, int W, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    numeric_dense_kernel(const int32_t* __restrict__ rows, DenseUnits U,
+                         const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
+                         const IT* __restrict__ ciA, const V* __restrict__ vA,
+                         const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
+                         const V* __restrict__ vB, long long n, int P,
+                         const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
+                         longlong2* __restrict__ arena, long long arena_stride,
+                         const int64_t* __restrict__ rpC, IT* __restrict__ ciC,
+                         V* __restrict__ vC, unsigned long long* work, int* err) {
+    constexpr bool HV = VOps<V>::has_val;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    constexpr size_t vbytes = HV ? sizeof(V) * W : 0;
+    unsigned char* base = smem_raw + (size_t)w * (vbytes + W / 8);
+    V* acc = reinterpret_cast<V*>(base);
+    unsigned* bm = reinterpret_cast<unsigned*>(base + vbytes);
+    longlong2* cursor = arena + ((long long)blockIdx.x * WARPS + w) * arena_stride;
+    for (int s = lane; s < W; s += 32)
+        if constexpr (HV) acc[s] = VOps<V>::init();
+    for (int s = lane; s < W / 32; s += 32) bm[s] = 0u;
+    __syncwarp();
+    const long long total_units = U.unit_begin[U.nclass];
+    while (true) {
+        long long u = 0;
+        if (lane == 0) u = (long long)atomicAdd(work, 1ull);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= total_units) break;
+        int b = 0;
+        while (b + 1 < U.nclass && U.unit_begin[b + 1] <= u) ++b;
+        const int G = U.G[b];
+        const long long local = u - U.unit_begin[b];
+        const long long r = U.row_begin[b] + local / G;
+        const int seg = (int)(local % G);
+        const int g0 = seg * (kSegGrid / G);
+        const int cs = (int)seg_chunk(g0, P);
+        const int ce = (int)seg_chunk(g0 + kSegGrid / G, P);
+        if (cs >= ce) continue;
+        const long long i = rows[r];
+        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        // output offset: row start plus the entries of the chunks before cs
+        long long before = 0;
+        for (int c = lane; c < cs; c += 32) before += chunkcnt[r * P + c];
+        before = warp_sum(before);
+        long long out = rpC[i] + before;
+        long long seg_total = 0;
+        for (int c = cs + lane; c < ce; c += 32) seg_total += chunkcnt[r * P + c];
+        seg_total = warp_sum(seg_total);
+        if (seg_total == 0) continue;
+        const long long out_end = out + seg_total;
+        // cursors at the segment start
+        for (long long p = a0 + lane; p < a1; p += 32) {
+            long long k = (long long)ciA[p];
+            long long s0 = rpB[k];
+            long long s1 = rpB[k + 1];
+            long long c0p = g0 == 0 ? s0 : s0 + segtab[k * (kSegGrid + 1) + g0];
+            cursor[p - a0] = make_longlong2(c0p, s1);
+        }
+        __syncwarp();
+        for (int c = cs; c < ce; ++c) {
+            if (chunkcnt[r * P + c] == 0) continue;
+            const long long c0 = (long long)c * W;
+            const long long c1 = min(c0 + (long long)W, n);
+            for (long long bb = a0; bb < a1; bb += 32) {
+                const int nb = (int)min(32LL, a1 - bb);
+                const long long p = bb + lane;
+                long long cur = 0;
+                V a = VOps<V>::init();
+                int len = 0;
+                if (lane < nb) {
+                    longlong2 ce2 = cursor[p - a0];
+                    cur = ce2.x;
+                    const long long end = ce2.y;
+                    a = load_val(vA, p);
+                    if (cur < end) {
+                        // length of the part of B(k,:) below c1, starting at the cursor:
+                        // four probes cover short parts, otherwise bisect
+                        const long long hi = min(cur + 32, end);
+                        IT pr0 = ciB[cur];
+                        IT pr1 = cur + 1 < hi ? ciB[cur + 1] : (IT)c1;
+                        IT pr2 = cur + 2 < hi ? ciB[cur + 2] : (IT)c1;
+                        IT pr3 = cur + 3 < hi ? ciB[cur + 3] : (IT)c1;
+                        IT prl = cur + 31 < end ? ciB[cur + 31] : (IT)c1;
+                        long long lo2, hi2;
+                        if ((long long)prl < c1) {
+                            lo2 = cur + 32;
+                            hi2 = end;
+                        } else if ((long long)pr3 >= c1 || cur + 4 >= hi) {
+                            lo2 = hi2 = cur + ((long long)pr0 < c1) + ((long long)pr1 < c1) +
+                                        ((long long)pr2 < c1) + ((long long)pr3 < c1);
+                        } else {
+                            lo2 = cur + 4;
+                            hi2 = hi;
+                        }
+                        while (lo2 < hi2) {
+                            long long mid = (lo2 + hi2) >> 1;
+                            if ((long long)ciB[mid] < c1) lo2 = mid + 1;
+                            else hi2 = mid;
+                        }
+                        len = (int)(lo2 - cur);
+                    }
+                }
+                const int incl = warp_incl_scan(len);
+                const int excl = incl - len;
+                const int total = __shfl_sync(kFull, incl, 31);
+                const int key = lane < nb ? excl : 0x7fffffff;
+                // flattened rounds over the batch's products in ascending k,
+                // four rounds per step so their loads overlap
+                for (int f0 = 0; f0 < total; f0 += 128) {
+                    long long jj[4];
+                    V bv[4];
+                    V av[4];
+                    bool vl[4];
+                    bool one_seg[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int fi = f0 + 32 * t + lane;
+                        int ee = 0;
+#pragma unroll
+                        for (int sb = 16; sb; sb >>= 1) {
+                            int kc = __shfl_sync(kFull, key, ee + sb);
+                            if (kc <= fi) ee += sb;
+                        }
+                        const long long qb = __shfl_sync(kFull, cur, ee);
+                        const int ex = __shfl_sync(kFull, excl, ee);
+                        av[t] = shfl_val(a, ee);
+                        vl[t] = fi < total;
+                        one_seg[t] = __shfl_sync(kFull, ee, 0) == __shfl_sync(kFull, ee, 31);
+                        const long long q = qb + (fi - ex);
+                        jj[t] = vl[t] ? (long long)ciB[q] : c0;
+                        bv[t] = vl[t] ? load_val(vB, q) : V{};
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int slot = (int)(jj[t] - c0);
+                        V v{};
+                        if (vl[t]) {
+                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                            v = VOps<V>::mul(av[t], bv[t]);
+                        }
+                        if (one_seg[t]) plain_add(acc, slot, vl[t], v);
+                        else ordered_add(acc, slot, vl[t], v);
+                    }
+                }
+                if (lane < nb && len) cursor[p - a0].x = cur + len;
+                __syncwarp();
+            }
+            // emit the chunk in column order (word by word of the presence
+            // bitmap, skipping empty words) and reset it
+            constexpr int NWORDS = W / 32;
+            for (int t0 = 0; t0 < NWORDS; t0 += 32) {
+                const int wi0 = t0 + lane;
+                const unsigned word = wi0 < NWORDS ? bm[wi0] : 0u;
+                unsigned nz = __ballot_sync(kFull, word != 0u);
+                while (nz) {
+                    const int wsel = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const unsigned wd = __shfl_sync(kFull, word, wsel);
+                    const bool bit = (wd >> lane) & 1u;
+                    const unsigned msk = __ballot_sync(kFull, bit);
+                    if (bit) {
+                        const int s = (t0 + wsel) * 32 + lane;
+                        const long long pos = out + __popc(msk & lanemask_lt());
+                        if (pos < out_end) {
+                            ciC[pos] = (IT)(c0 + s);
+                            if constexpr (HV) vC[pos] = acc[s];
+                        }
+                        if constexpr (HV) acc[s] = VOps<V>::init();
+                    }
+                    out += __popc(msk);
+                }
+                if (wi0 < NWORDS) bm[wi0] = 0u;
+            }
+            __syncwarp();
+        }
+        if (lane == 0 && out != out_end) atomicExch(err, (int)kDevCountMismatch);
+    }
+}
+
+// ------------------------------------------------------------ k-slices
+// bounds[s*m + i] = first position in A(i,:) with column >= floor(s*l/c).
+template <class IT>
+__global__ void kslice_bounds_kernel(long long m, long long l, int c,
+                                     const int64_t* __restrict__ rp, const IT* __restrict__ ci,
+                                     int64_t* __restrict__ bounds) {
+    const long long total = m * (long long)(c + 1);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long s = t / m, i = t - s * m;
+        const long long key = (s * l) / c;
+        long long lo = rp[i], hi = rp[i + 1];
+        while (lo < hi) {
+            long long mid = (lo + hi) >> 1;
+            if ((long long)ci[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        bounds[t] = lo;
+    }
+}
+
+}  // namespace sg

@@ -1,0 +1,334 @@
+"""Python binding of the C ABI in include/spgemm.h (ctypes).
+
+Argument marshalling only: every step of the product runs in the CUDA
+library.  PyTorch supplies device memory (outputs and workspaces are torch
+tensors) and the stream (the current torch stream).  If the library cannot
+be loaded the import fails; there is no CPU fallback.
+
+Names follow the C entry points: ``plan``, ``symbolic``, ``numeric``,
+``kslice_bounds``, ``merge_symbolic``, ``merge_numeric``; ``spgemm`` and
+``spgemm_kslice`` chain them for the common case."""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+F64, F32, I64, BOOL = 0, 1, 2, 3
+INDEX_I32, INDEX_I64 = 0, 1
+PLUS_TIMES, OR_AND = 0, 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_CSR", 3: "INDEX_OVERFLOW", 4: "OUT_OF_MEMORY",
+          5: "TIMEOUT", 6: "CUDA", 7: "NOT_SUPPORTED", 8: "INTERNAL"}
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("rowend", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("index_type", ctypes.c_int32), ("value_type", ctypes.c_int32)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("semiring", ctypes.c_int32), ("checked", ctypes.c_int32),
+                ("dense_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("m", "l", "n", "flops", "max_row_flops", "rows_empty", "rows_hash",
+                 "rows_dense", "chunk_width", "chunks_per_row", "nnz_c")]
+
+
+def _load():
+    path = _build.LIB
+    if not _build.up_to_date():
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    P, S, I64_, I32_ = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int32
+    st = ctypes.c_int
+    sig = {
+        "spgemm_version": (ctypes.c_char_p, []),
+        "spgemm_kernel_launches": (I64_, []),
+        "spgemm_last_error": (ctypes.c_char_p, []),
+        "spgemm_plan_workspace_size": (S, [I64_]),
+        "spgemm_plan": (st, [P, P, P, P, P, S, P]),
+        "spgemm_plan_info": (st, [P, P]),
+        "spgemm_workspace_size": (st, [P, P]),
+        "spgemm_symbolic": (st, [P, P, S, P, P]),
+        "spgemm_numeric": (st, [P, P, S, P, P, P]),
+        "spgemm_check": (st, [P]),
+        "spgemm_plan_destroy": (None, [P]),
+        "spgemm_kslice_bounds": (st, [P, I32_, P, P]),
+        "spgemm_merge_workspace_size": (S, [I32_, I64_, I64_]),
+        "spgemm_merge_symbolic": (st, [I32_, P, P, P, P, S, P, P]),
+        "spgemm_merge_numeric": (st, [I32_, P, P, P, P, S, P, P, P]),
+        "spgemm_merge_check": (st, [P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIBRARY_PATH = _build.LIB
+
+
+def version() -> str:
+    return _lib.spgemm_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in this process."""
+    return int(_lib.spgemm_kernel_launches())
+
+
+def _check(status: int):
+    if status != 0:
+        raise SpgemmError(status, _lib.spgemm_last_error().decode())
+
+
+@dataclasses.dataclass
+class DeviceCSR:
+    """CSR on the GPU: rowptr int64 [nrows+1] (or per-row starts when rowend
+    is given), col int32/int64, val float64/float32/int64 or None."""
+
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor
+    col: torch.Tensor
+    val: Optional[torch.Tensor]
+    rowend: Optional[torch.Tensor] = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def index_type(self) -> int:
+        return INDEX_I32 if self.col.dtype == torch.int32 else INDEX_I64
+
+    @property
+    def value_type(self) -> int:
+        if self.val is None:
+            return BOOL
+        return {torch.float64: F64, torch.float32: F32, torch.int64: I64}[self.val.dtype]
+
+    def to_host(self):
+        """Returns (rowptr, col, val) numpy arrays (rowptr always plain CSR)."""
+        rp = self.rowptr.cpu().numpy()
+        col = self.col.cpu().numpy()
+        val = None if self.val is None else self.val.cpu().numpy()
+        return rp, col, val
+
+
+def to_device(M, device="cuda") -> DeviceCSR:
+    """Copies a host CSR (any object with nrows, ncols, rowptr, col, val)."""
+    val = None if M.val is None else torch.from_numpy(np.ascontiguousarray(M.val)).to(device)
+    return DeviceCSR(int(M.nrows), int(M.ncols),
+                     torch.from_numpy(np.ascontiguousarray(M.rowptr, dtype=np.int64)).to(device),
+                     torch.from_numpy(np.ascontiguousarray(M.col)).to(device), val)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None or t.numel() == 0 and t.data_ptr() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _csr(M: DeviceCSR, value_type: Optional[int] = None) -> _Csr:
+    for t in (M.rowptr, M.col, M.val, M.rowend):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("CSR arrays must be contiguous CUDA tensors")
+    return _Csr(M.nrows, M.ncols, M.nnz if M.rowend is None else int(M.col.numel()),
+                M.rowptr.data_ptr(), None if M.rowend is None else M.rowend.data_ptr(),
+                M.col.data_ptr() if M.col.numel() else None,
+                None if M.val is None or M.val.numel() == 0 else M.val.data_ptr(),
+                M.index_type, M.value_type if value_type is None else value_type)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+class Plan:
+    """A planned product C = A.B (spgemm_plan); keeps A, B and its
+    workspaces alive until closed."""
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES,
+                 checked: bool = False, stream=None, dense_chunk: int = 0):
+        self.A, self.B = A, B
+        self.device = A.rowptr.device
+        self._cA, self._cB = _csr(A), _csr(B)
+        self._opts = _Opts(semiring, 1 if checked else 0, dense_chunk)
+        self.pattern_only = semiring == OR_AND or A.val is None
+        self.stream = stream
+        self._plan_ws = _workspace(_lib.spgemm_plan_workspace_size(A.nrows), self.device)
+        h = ctypes.c_void_p()
+        _check(_lib.spgemm_plan(ctypes.byref(self._cA), ctypes.byref(self._cB),
+                                ctypes.byref(self._opts), _stream(stream),
+                                ctypes.c_void_p(self._plan_ws.data_ptr()),
+                                self._plan_ws.numel(), ctypes.byref(h)))
+        self._h = h
+        nb = ctypes.c_size_t()
+        _check(_lib.spgemm_workspace_size(self._h, ctypes.byref(nb)))
+        self.ws = _workspace(nb.value, self.device)
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(_lib.spgemm_plan_info(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.spgemm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool = False,
+         stream=None, dense_chunk: int = 0) -> Plan:
+    return Plan(A, B, semiring, checked, stream, dense_chunk)
+
+
+def symbolic(p: Plan, rowptrC: Optional[torch.Tensor] = None):
+    """Row pointers of C and nnz(C) (waits for the stream)."""
+    if rowptrC is None:
+        rowptrC = torch.empty(p.A.nrows + 1, dtype=torch.int64, device=p.device)
+    nnz = ctypes.c_int64()
+    _check(_lib.spgemm_symbolic(p._h, ctypes.c_void_p(p.ws.data_ptr()), p.ws.numel(),
+                                ctypes.c_void_p(rowptrC.data_ptr()), ctypes.byref(nnz)))
+    return rowptrC, int(nnz.value)
+
+
+def numeric(p: Plan, rowptrC: torch.Tensor, colC: torch.Tensor,
+            valC: Optional[torch.Tensor]) -> None:
+    _check(_lib.spgemm_numeric(p._h, ctypes.c_void_p(p.ws.data_ptr()), p.ws.numel(),
+                               ctypes.c_void_p(rowptrC.data_ptr()),
+                               ctypes.c_void_p(colC.data_ptr()) if colC.numel() else None,
+                               None if valC is None or valC.numel() == 0
+                               else ctypes.c_void_p(valC.data_ptr())))
+
+
+def check(p: Plan) -> None:
+    _check(_lib.spgemm_check(p._h))
+
+
+def alloc_output(p: Plan, nnz: int):
+    colC = torch.empty(nnz, dtype=p.A.col.dtype, device=p.device)
+    valC = None if p.pattern_only else torch.empty(nnz, dtype=p.A.val.dtype, device=p.device)
+    return colC, valC
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool = False,
+           stream=None, verify: bool = False, dense_chunk: int = 0) -> DeviceCSR:
+    """C = A.B: plan, symbolic, allocate C, numeric."""
+    p = plan(A, B, semiring, checked, stream, dense_chunk)
+    rowptrC, nnz = symbolic(p)
+    colC, valC = alloc_output(p, nnz)
+    numeric(p, rowptrC, colC, valC)
+    if verify:
+        check(p)
+    p.close()
+    return DeviceCSR(A.nrows, B.ncols, rowptrC, colC, valC)
+
+
+def kslice_bounds(A: DeviceCSR, c: int, stream=None) -> torch.Tensor:
+    """(c+1) x m int64: slice s of row i is [b[s, i], b[s+1, i])."""
+    b = torch.empty((c + 1, A.nrows), dtype=torch.int64, device=A.rowptr.device)
+    cA = _csr(A)
+    _check(_lib.spgemm_kslice_bounds(ctypes.byref(cA), c, _stream(stream),
+                                     ctypes.c_void_p(b.data_ptr()) if b.numel() else None))
+    return b
+
+
+def kslice_views(A: DeviceCSR, c: int, stream=None) -> List[DeviceCSR]:
+    b = kslice_bounds(A, c, stream)
+    return [DeviceCSR(A.nrows, A.ncols, b[s], A.col, A.val, rowend=b[s + 1]) for s in range(c)]
+
+
+def _parts(parts: Sequence[DeviceCSR]):
+    arr = (_Csr * len(parts))(*[_csr(P) for P in parts])
+    return arr
+
+
+def merge_workspace(c: int, m: int, n: int, device) -> torch.Tensor:
+    return _workspace(_lib.spgemm_merge_workspace_size(c, m, n), device)
+
+
+def merge_symbolic(parts: Sequence[DeviceCSR], ws: torch.Tensor, semiring: int = PLUS_TIMES,
+                   stream=None, rowptrC: Optional[torch.Tensor] = None):
+    m = parts[0].nrows
+    if rowptrC is None:
+        rowptrC = torch.empty(m + 1, dtype=torch.int64, device=ws.device)
+    arr = _parts(parts)
+    opts = _Opts(semiring, 0)
+    nnz = ctypes.c_int64()
+    _check(_lib.spgemm_merge_symbolic(len(parts), arr, ctypes.byref(opts), _stream(stream),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      ctypes.c_void_p(rowptrC.data_ptr()), ctypes.byref(nnz)))
+    return rowptrC, int(nnz.value)
+
+
+def merge_numeric(parts: Sequence[DeviceCSR], ws: torch.Tensor, rowptrC: torch.Tensor,
+                  colC: torch.Tensor, valC: Optional[torch.Tensor], semiring: int = PLUS_TIMES,
+                  stream=None) -> None:
+    arr = _parts(parts)
+    opts = _Opts(semiring, 0)
+    _check(_lib.spgemm_merge_numeric(len(parts), arr, ctypes.byref(opts), _stream(stream),
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                     ctypes.c_void_p(rowptrC.data_ptr()),
+                                     ctypes.c_void_p(colC.data_ptr()) if colC.numel() else None,
+                                     None if valC is None or valC.numel() == 0
+                                     else ctypes.c_void_p(valC.data_ptr())))
+
+
+def merge_check(ws: torch.Tensor, stream=None) -> None:
+    _check(_lib.spgemm_merge_check(_stream(stream), ctypes.c_void_p(ws.data_ptr())))
+
+
+def merge(parts: Sequence[DeviceCSR], semiring: int = PLUS_TIMES, stream=None,
+          verify: bool = False) -> DeviceCSR:
+    m, n = parts[0].nrows, parts[0].ncols
+    ws = merge_workspace(len(parts), m, n, parts[0].rowptr.device)
+    rowptrC, nnz = merge_symbolic(parts, ws, semiring, stream)
+    pattern = semiring == OR_AND or parts[0].val is None
+    colC = torch.empty(nnz, dtype=parts[0].col.dtype, device=ws.device)
+    valC = None if pattern else torch.empty(nnz, dtype=parts[0].val.dtype, device=ws.device)
+    merge_numeric(parts, ws, rowptrC, colC, valC, semiring, stream)
+    if verify:
+        merge_check(ws, stream)
+    return DeviceCSR(m, n, rowptrC, colC, valC)
+
+
+def spgemm_kslice(A: DeviceCSR, B: DeviceCSR, c: int, semiring: int = PLUS_TIMES,
+                  stream=None, verify: bool = False):
+    """The k-split product: C_s = A(:,K_s).B for the c contiguous slices K_s
+    of the inner dimension, then C = sum_s C_s by the merge.  Returns
+    (C, partials)."""
+    parts = [spgemm(As, B, semiring, stream=stream, verify=verify)
+             for As in kslice_views(A, c, stream)]
+    return merge(parts, semiring, stream, verify), parts
