@@ -1,0 +1,383 @@
+"""Benchmark of the sparse product C = A.A on R-MAT scale 18 (Graph500
+parameters a=.57, b=c=.19, d=.05, edge factor 16, symmetrised, duplicates
+summed, randomly permuted, float64 values U(0,1), int32 column indices).
+
+One step = the whole plain two-phase path through the library: row analysis
+and binning (spgemm_plan), symbolic phase and row pointers (spgemm_symbolic),
+allocation of C, numeric phase (spgemm_numeric).  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (a 256 MiB write) between steps,
+outside the timed events.  value = 2 * flops / time (GFLOP/s).
+
+--impl reference times the CPU oracle (plain Gustavson with a dense
+accumulator, all host cores) on a bounded sample of rows of the same
+workload, with the same metric.
+
+Multi-GPU (torchrun, N ranks): each rank multiplies a contiguous row panel of
+A by the full A (rows are independent; no collective on the data path);
+value = total flops of all ranks / max rank time ("scaling": "strong")."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpGEMM GFLOP/s + HBM-roofline %, learned/batched vs plain 2-phase, 1 GB300"
+UNIT = "GFLOP/s"
+SCALE = 18
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def algorithmic_bytes(A, nnz_c: int):
+    """Bytes the plain two-phase method must move (symbolic + numeric):
+    symbolic reads rowptr/col of A and B and writes rowptr(C); numeric reads
+    rowptr/col/val of A and B and rowptr(C) and writes col/val of C."""
+    m, nnzA = A.nrows, A.nnz
+    idx, v, r = A.col.dtype.itemsize, 8, 8
+    a_idx = r * (m + 1) + idx * nnzA
+    sym = 2 * a_idx + 8 * (m + 1)
+    num = 2 * (a_idx + v * nnzA) + 8 * (m + 1) + (idx + v) * nnz_c
+    return sym, num
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of numeric_dense_kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "numeric_dense_rmat18.md")
+    src = os.path.join(ROOT, "paper_1510_00844_gb300", "csrc", "kernels.cuh")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if f"`{digest}`" not in text:
+        return None
+    for ln in text.splitlines():
+        if ln.startswith("traffic_bytes_per_launch_rmat18:"):
+            return int(ln.split(":")[1])
+    return None
+
+
+def panel(m: int, world: int, rank: int):
+    return (m * rank) // world, (m * (rank + 1)) // world
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1510_00844_gb300 import inputs
+    from paper_1510_00844_gb300 import spgemm as sg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    A = inputs.rmat(SCALE)
+    dA = sg.to_device(A, dev)
+    r0, r1 = panel(A.nrows, world, rank)
+    # row panel of A as a view on its own arrays (rowptr slice + rowend)
+    dP = sg.DeviceCSR(r1 - r0, A.ncols, dA.rowptr[r0:r1], dA.col, dA.val,
+                      rowend=dA.rowptr[r0 + 1:r1 + 1]) if world > 1 else dA
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        p = sg.plan(dP, dA)
+        rowptrC, nnz = sg.symbolic(p)
+        colC, valC = sg.alloc_output(p, nnz)
+        if ev is not None:
+            ev[0].record(stream)
+        sg.numeric(p, rowptrC, colC, valC)
+        if ev is not None:
+            ev[1].record(stream)
+        return p, rowptrC, colC, valC, nnz
+
+    for _ in range(args.warmup):
+        out = step()
+        del out
+    torch.cuda.synchronize()
+    info = None
+    step_ms, num_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sg.kernel_launches()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        e0.record(stream)
+        p, rowptrC, colC, valC, nnz = step(ev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        num_ms.append(ev[0].elapsed_time(ev[1]))
+        info = p.info()
+        del p, rowptrC, colC, valC
+    torch.cuda.synchronize()
+    launches = sg.kernel_launches() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(np.sum(step_ms))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    fl = torch.tensor([float(info["flops"])], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(fl, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    flops_all = float(fl.item())
+    ms_per_step = total_ms / args.steps
+    value = 2.0 * flops_all / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the numeric phase (numeric_dense_kernel is ~99% of it)
+    nnz_c = int(info["nnz_c"])
+    _, num_bytes = algorithmic_bytes(A, nnz_c)
+    num_avg = float(np.mean(num_ms))
+    hbm, peak_src = peaks()
+    achieved = num_bytes / (num_avg * 1e-3) / 1e9
+    traffic = profiled_traffic()
+
+    e2e = (run_e2e(args, A, sg, torch, dev, dP if world == 1 else None)
+           if rank == 0 and not args.no_e2e else None)
+    cpu = run_cpu_baseline(A) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded R-MAT generator; no dataset)",
+            "config": {"workload": "rmat18_g500_squared", "scale": SCALE, "edge_factor": 16,
+                       "n": A.nrows, "nnz_A": A.nnz, "flops": int(flops_all // 1),
+                       "nnz_C": nnz_c, "index": "int32", "values": "f64",
+                       "path": "plain two-phase", "l2": "flushed between steps",
+                       "parallelism": f"row panels x{world}"},
+            "phases_ms": {"numeric": round(num_avg, 3), "step": round(ms_per_step, 3)},
+            "roofline": {"bound": "hbm", "kernel": "numeric phase (numeric_dense_kernel)",
+                         "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "peak_source": peak_src,
+                         "algorithmic_bytes": num_bytes, "traffic": traffic},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, A, sg, torch, dev, dP):
+    """Same metric through the public API from pinned host buffers: H2D of
+    A, plan + symbolic + numeric, D2H of C (row pointers, columns, values)."""
+    if dP is None:
+        return None
+    hr = torch.from_numpy(A.rowptr).pin_memory()
+    hc = torch.from_numpy(A.col).pin_memory()
+    hv = torch.from_numpy(A.val).pin_memory()
+    dr = torch.empty_like(hr, device=dev)
+    dc = torch.empty_like(hc, device=dev)
+    dv = torch.empty_like(hv, device=dev)
+    out_host = None
+    times = []
+    h2d = hr.numel() * 8 + hc.numel() * hc.element_size() + hv.numel() * 8
+    d2h = 0
+    nsteps = max(1, min(args.steps, 2))
+    for it in range(1 + nsteps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dr.copy_(hr, non_blocking=True)
+        dc.copy_(hc, non_blocking=True)
+        dv.copy_(hv, non_blocking=True)
+        M = sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)
+        C = sg.spgemm(M, M)
+        if out_host is None:
+            out_host = (torch.empty(C.rowptr.numel(), dtype=torch.int64, pin_memory=True),
+                        torch.empty(C.col.numel(), dtype=C.col.dtype, pin_memory=True),
+                        torch.empty(C.val.numel(), dtype=torch.float64, pin_memory=True))
+        out_host[0].copy_(C.rowptr, non_blocking=True)
+        out_host[1].copy_(C.col, non_blocking=True)
+        out_host[2].copy_(C.val, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d2h = C.rowptr.numel() * 8 + C.col.numel() * C.col.element_size() + C.val.numel() * 8
+        if it > 0:
+            times.append(t1 - t0)
+        del C, M
+    fl = sg.plan(sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv),
+                 sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)).info()["flops"]
+    sec = float(np.mean(times))
+    return {"value": round(2.0 * fl / sec / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": round(sec * 1e3, 3), "steps": nsteps}
+
+
+def oracle_sample(A, target_flops):
+    """Rows of A chosen by a seeded permutation until their flops reach
+    target_flops (a bounded sample with the workload's row mix)."""
+    import oracle
+    fl = oracle.row_flops(A, A)
+    order = np.random.default_rng(11).permutation(A.nrows)
+    cum = np.cumsum(fl[order])
+    k = int(np.searchsorted(cum, target_flops)) + 1
+    rows = np.sort(order[:k])
+    lens = A.rowptr[rows + 1] - A.rowptr[rows]
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows])
+    sub = oracle.OCSR(len(rows), A.ncols, rp, A.col[idx].astype(np.int64), A.val[idx])
+    return sub, int(fl[rows].sum()), len(rows)
+
+
+def run_cpu_baseline(A, target_flops=3e9, reps=1):
+    import oracle
+    sub, sflops, nrows = oracle_sample(A, target_flops)
+    threads = len(os.sched_getaffinity(0))
+    oracle.spgemm(oracle.OCSR(1, A.ncols, sub.rowptr[:2], sub.col, sub.val), A,
+                  nthreads=threads)   # warm the library
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.spgemm(sub, A, nthreads=threads)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return {"value": round(2.0 * sflops / best / 1e9, 4), "unit": UNIT,
+            "cores": oracle.num_threads(threads), "kind": "oracle",
+            "sample": f"{nrows} seeded random rows of A (flops {sflops}) times A; "
+                      f"{best:.2f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1510_00844_gb300 import inputs
+    import oracle
+    A = inputs.rmat(SCALE)
+    threads = len(os.sched_getaffinity(0))
+    sub, sflops, nrows = oracle_sample(A, 1e9)
+    for _ in range(args.warmup):
+        oracle.spgemm(sub, A, nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.spgemm(sub, A, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = float(np.mean(times)) * 1e3
+    value = 2.0 * sflops / (ms * 1e-3) / 1e9
+    cores = oracle.num_threads(threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded R-MAT generator; no dataset)",
+        "config": {"workload": "rmat18_g500_squared", "scale": SCALE, "edge_factor": 16,
+                   "index": "int32", "values": "f64", "path": "CPU oracle (dense-accumulator Gustavson)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nrows} seeded random rows of A (flops {sflops}) times A per step"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

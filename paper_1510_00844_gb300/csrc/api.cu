@@ -87,11 +87,13 @@ WsLayout workspace_layout(const Plan& P) {
     off += align_up((size_t)P.ndense * (size_t)P.P * sizeof(int32_t));
     L.segtab = off;
     if (P.ndense > 0) off += align_up((size_t)P.l * (kSegGrid + 1) * sizeof(int32_t));
+    L.runlen = off;
+    if (P.ndense > 0) off += align_up((size_t)P.B.nnz * sizeof(int32_t));
     L.arena = off;
     L.arena_stride = std::max<long long>(1, P.max_dense_len);
     if (P.ndense > 0)
         off += align_up((size_t)P.dense_grid * P.dense_warps_per_block * (size_t)L.arena_stride *
-                        sizeof(longlong2));
+                        sizeof(DenseCursor));
     L.scan = off;
     off += align_up(scan_temp_bytes(P.m + 1));
     L.total = off;

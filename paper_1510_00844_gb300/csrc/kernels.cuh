@@ -413,6 +413,50 @@ __host__ __device__ __forceinline__ long long seg_chunk(int g, int P) {
     return ((long long)g * P) / kSegGrid;
 }
 
+// Where a warp stands in B(k,:) while it sweeps the chunks of a row: the
+// position, the entries left in the row, and the column at the position
+// (INT_MAX when none), so a chunk with nothing of B(k,:) costs one load.
+struct __align__(16) DenseCursor {
+    long long pos;
+    int left;
+    int next_col;
+};
+
+// runlen[q] = number of entries from q to the end of q's column chunk
+// (col / W) inside its row of B: the length of the part of B(k,:) that a
+// chunk sweep consumes in one step.  One warp per row, windows of 32 from the
+// row end backwards.
+template <class IT>
+__global__ void runlen_kernel(long long l, const int64_t* __restrict__ rpB,
+                              const IT* __restrict__ ciB, int W, int32_t* __restrict__ runlen) {
+    const int lane = lane_id();
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < l; k += nwarps) {
+        const long long s0 = rpB[k], s1 = rpB[k + 1];
+        long long carry_end = s1;          // run end of the window after this one
+        long long carry_chunk = -1;        // chunk of the first entry of that window
+        for (long long hi = s1; hi > s0; hi -= 32) {
+            const long long lo = max(s0, hi - 32);
+            const long long q = lo + lane;
+            const bool in = q < hi;
+            const long long ch = in ? (long long)ciB[q] / W : -2;
+            long long nxt = __shfl_down_sync(kFull, ch, 1);
+            if (lane == 31 || q + 1 >= hi) nxt = carry_chunk;
+            const bool last = in && nxt != ch;   // q ends its run inside this window
+            const unsigned lm = __ballot_sync(kFull, last);
+            const unsigned ge = lm & (0xffffffffu << lane);
+            long long end;
+            if (ge) end = lo + (__ffs(ge) - 1) + 1;
+            else end = carry_end;
+            if (in) runlen[q] = (int32_t)(end - q);
+            // first entry of this window seeds the carry for the window before it
+            carry_end = __shfl_sync(kFull, end, 0);
+            carry_chunk = __shfl_sync(kFull, ch, 0);
+        }
+    }
+}
+
 // segtab[k * (kSegGrid+1) + g] = first position p in B(k,:) with col >= seg_chunk(g)*W,
 // relative to rowptr[k].
 template <class IT>
@@ -444,7 +488,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                          const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
                          const V* __restrict__ vB, long long n, int P,
                          const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
-                         longlong2* __restrict__ arena, long long arena_stride,
+                         const int32_t* __restrict__ runlen, DenseCursor* __restrict__ arena,
+                         long long arena_stride,
                          const int64_t* __restrict__ rpC, IT* __restrict__ ciC,
                          V* __restrict__ vC, unsigned long long* work, int* err) {
     constexpr bool HV = VOps<V>::has_val;
@@ -455,7 +500,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     unsigned char* base = smem_raw + (size_t)w * (vbytes + W / 8);
     V* acc = reinterpret_cast<V*>(base);
     unsigned* bm = reinterpret_cast<unsigned*>(base + vbytes);
-    longlong2* cursor = arena + ((long long)blockIdx.x * WARPS + w) * arena_stride;
+    DenseCursor* cursor = arena + ((long long)blockIdx.x * WARPS + w) * arena_stride;
     for (int s = lane; s < W; s += 32)
         if constexpr (HV) acc[s] = VOps<V>::init();
     for (int s = lane; s < W / 32; s += 32) bm[s] = 0u;
@@ -494,7 +539,11 @@ __global__ void __launch_bounds__(WARPS * 32)
             long long s0 = rpB[k];
             long long s1 = rpB[k + 1];
             long long c0p = g0 == 0 ? s0 : s0 + segtab[k * (kSegGrid + 1) + g0];
-            cursor[p - a0] = make_longlong2(c0p, s1);
+            DenseCursor nc;
+            nc.pos = c0p;
+            nc.left = (int)(s1 - c0p);
+            nc.next_col = nc.left > 0 ? (int)ciB[c0p] : 0x7fffffff;
+            cursor[p - a0] = nc;
         }
         __syncwarp();
         for (int c = cs; c < ce; ++c) {
@@ -504,42 +553,18 @@ __global__ void __launch_bounds__(WARPS * 32)
             for (long long bb = a0; bb < a1; bb += 32) {
                 const int nb = (int)min(32LL, a1 - bb);
                 const long long p = bb + lane;
-                long long cur = 0;
-                V a = VOps<V>::init();
+                DenseCursor cs2{0, 0, 0x7fffffff};
+                if (lane < nb) cs2 = cursor[p - a0];
+                const bool here = lane < nb && (long long)cs2.next_col < c1;
+                if (__ballot_sync(kFull, here) == 0u) continue;
+                // the part of B(k,:) inside this chunk: runlen entries from the cursor
                 int len = 0;
-                if (lane < nb) {
-                    longlong2 ce2 = cursor[p - a0];
-                    cur = ce2.x;
-                    const long long end = ce2.y;
+                V a = VOps<V>::init();
+                if (here) {
+                    len = runlen[cs2.pos];
                     a = load_val(vA, p);
-                    if (cur < end) {
-                        // length of the part of B(k,:) below c1, starting at the cursor:
-                        // four probes cover short parts, otherwise bisect
-                        const long long hi = min(cur + 32, end);
-                        IT pr0 = ciB[cur];
-                        IT pr1 = cur + 1 < hi ? ciB[cur + 1] : (IT)c1;
-                        IT pr2 = cur + 2 < hi ? ciB[cur + 2] : (IT)c1;
-                        IT pr3 = cur + 3 < hi ? ciB[cur + 3] : (IT)c1;
-                        IT prl = cur + 31 < end ? ciB[cur + 31] : (IT)c1;
-                        long long lo2, hi2;
-                        if ((long long)prl < c1) {
-                            lo2 = cur + 32;
-                            hi2 = end;
-                        } else if ((long long)pr3 >= c1 || cur + 4 >= hi) {
-                            lo2 = hi2 = cur + ((long long)pr0 < c1) + ((long long)pr1 < c1) +
-                                        ((long long)pr2 < c1) + ((long long)pr3 < c1);
-                        } else {
-                            lo2 = cur + 4;
-                            hi2 = hi;
-                        }
-                        while (lo2 < hi2) {
-                            long long mid = (lo2 + hi2) >> 1;
-                            if ((long long)ciB[mid] < c1) lo2 = mid + 1;
-                            else hi2 = mid;
-                        }
-                        len = (int)(lo2 - cur);
-                    }
                 }
+                const long long cur = cs2.pos;
                 const int incl = warp_incl_scan(len);
                 const int excl = incl - len;
                 const int total = __shfl_sync(kFull, incl, 31);
@@ -582,34 +607,38 @@ __global__ void __launch_bounds__(WARPS * 32)
                         else ordered_add(acc, slot, vl[t], v);
                     }
                 }
-                if (lane < nb && len) cursor[p - a0].x = cur + len;
+                if (here) {
+                    DenseCursor nc;
+                    nc.pos = cs2.pos + len;
+                    nc.left = cs2.left - len;
+                    nc.next_col = nc.left > 0 ? (int)ciB[nc.pos] : 0x7fffffff;
+                    cursor[p - a0] = nc;
+                }
                 __syncwarp();
             }
-            // emit the chunk in column order (word by word of the presence
-            // bitmap, skipping empty words) and reset it
+            // emit the chunk in column order: lane t owns bitmap word t (32
+            // columns), a warp scan of the popcounts gives each lane its output
+            // run; words and values are reset on the way
             constexpr int NWORDS = W / 32;
             for (int t0 = 0; t0 < NWORDS; t0 += 32) {
                 const int wi0 = t0 + lane;
-                const unsigned word = wi0 < NWORDS ? bm[wi0] : 0u;
-                unsigned nz = __ballot_sync(kFull, word != 0u);
-                while (nz) {
-                    const int wsel = __ffs(nz) - 1;
-                    nz &= nz - 1;
-                    const unsigned wd = __shfl_sync(kFull, word, wsel);
-                    const bool bit = (wd >> lane) & 1u;
-                    const unsigned msk = __ballot_sync(kFull, bit);
-                    if (bit) {
-                        const int s = (t0 + wsel) * 32 + lane;
-                        const long long pos = out + __popc(msk & lanemask_lt());
-                        if (pos < out_end) {
-                            ciC[pos] = (IT)(c0 + s);
-                            if constexpr (HV) vC[pos] = acc[s];
-                        }
-                        if constexpr (HV) acc[s] = VOps<V>::init();
+                unsigned word = wi0 < NWORDS ? bm[wi0] : 0u;
+                const int pc = __popc(word);
+                const int pincl = warp_incl_scan(pc);
+                long long pos = out + (pincl - pc);
+                while (word) {
+                    const int bit = __ffs(word) - 1;
+                    word &= word - 1;
+                    const int s = wi0 * 32 + bit;
+                    if (pos < out_end) {
+                        ciC[pos] = (IT)(c0 + s);
+                        if constexpr (HV) vC[pos] = acc[s];
                     }
-                    out += __popc(msk);
+                    if constexpr (HV) acc[s] = VOps<V>::init();
+                    ++pos;
                 }
                 if (wi0 < NWORDS) bm[wi0] = 0u;
+                out += __shfl_sync(kFull, pincl, 31);
             }
             __syncwarp();
         }

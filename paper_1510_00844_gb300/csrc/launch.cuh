@@ -101,6 +101,11 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
         segtab_kernel<IT><<<(unsigned)g, 256, 0, P.stream>>>(P.l, P.B.rowptr, (const IT*)P.B.col,
                                                              P.W, P.P, (int32_t*)(ws + L.segtab));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        long long g2 = grid_for(P.l, 8, P.sm_count, 8);
+        count_launches(1);
+        runlen_kernel<IT><<<(unsigned)g2, 256, 0, P.stream>>>(P.l, P.B.rowptr, (const IT*)P.B.col,
+                                                              P.W, (int32_t*)(ws + L.runlen));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (P.ndense > 0) {
         auto k = symbolic_dense_kernel<IT>;
@@ -177,8 +182,8 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
         P.rows + P.class_off[kClassDense0], P.units, P.A.rowptr, P.A.rowend,
         (const IT*)P.A.col, (const V*)P.A.val, P.B.rowptr, (const IT*)P.B.col,
         (const V*)P.B.val, P.n, P.P, (const int32_t*)(ws + L.chunkcnt),
-        (const int32_t*)(ws + L.segtab), (longlong2*)(ws + L.arena), L.arena_stride, rpC,
-        colC, valC, work, &P.cnt->err);
+        (const int32_t*)(ws + L.segtab), (const int32_t*)(ws + L.runlen),
+        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, colC, valC, work, &P.cnt->err);
     return cudaGetLastError();
 }
 

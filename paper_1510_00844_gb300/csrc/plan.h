@@ -47,7 +47,7 @@ namespace sg {
 void count_launches(long long k);
 
 struct WsLayout {
-    size_t chunkcnt = 0, segtab = 0, arena = 0, scan = 0, total = 0;
+    size_t chunkcnt = 0, segtab = 0, runlen = 0, arena = 0, scan = 0, total = 0;
     long long arena_stride = 0;
 };
 void build_dense_units(Plan& P);
