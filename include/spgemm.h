@@ -191,6 +191,24 @@ spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spg
                                    void* stream, void* ws, size_t ws_bytes,
                                    const int64_t* rowptrC, void* colC, void* valC);
 
+/* spgemm_merge_symbolic_static -- the paper has no counterpart: this is an
+ * interface variant.  Same result as spgemm_merge_symbolic (rowptrC of
+ * C = sum_s parts[s] and nnz(C) on the host; waits for the stream) for callers
+ * that may not allocate device memory and have no workspace to pass: code
+ * that runs under a fixed device-memory budget reserved at start-up, or a
+ * plug-in interface that hands over only inputs and outputs.  It allocates
+ * nothing: its scratch (error word and scan partial sums, about 33 KB) is one
+ * file-scope device array that every GPU loading the library keeps until the
+ * process exits.
+ * Limits: at most 2^24 rows (INVALID_ARG beyond).  All calls on a device
+ * share the array, which keeps the last call's contents (the error word is
+ * cleared at the start of each call); calls that overlap on the GPU race on
+ * it.  The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture. */
+spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
+                                           const spgemm_opts* opts, void* stream,
+                                           int64_t* rowptrC, int64_t* nnz_c);
+
 /* Reads the device error word the merge calls record in `ws` (waits for the
  * stream); SPGEMM_ERR_INTERNAL if a row's emitted count disagreed with
  * rowptrC. */

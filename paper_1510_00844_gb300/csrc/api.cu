@@ -79,6 +79,7 @@ namespace sg {
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_last_error = msg; }
 
 WsLayout workspace_layout(const Plan& P) {
     WsLayout L;

@@ -28,9 +28,6 @@ __global__ void bin_rows_kernel(long long m, long long n, long long max_dense_n,
 
 // ------------------------------------------------------------------ scan
 // In-place exclusive scan of int64 x[0..N).  Tiles of 4096 (256 x 16).
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;
 
 __global__ void scan_reduce_kernel(const int64_t* __restrict__ x, long long N,
                                    int64_t* __restrict__ part) {

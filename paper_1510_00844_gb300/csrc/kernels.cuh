@@ -42,6 +42,11 @@ struct DevCounters {
     int pad[30];
 };
 
+// Tile of the int64 exclusive scan: 256 threads x 16 items.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
 __host__ __device__ __forceinline__ int row_class(long long flops, long long n, long long max_dense_n,
                                                    int* unsupported) {
     if (flops == 0) return kClassEmpty;

@@ -1,0 +1,115 @@
+// spgemm_merge_symbolic_static: the row-count step of the k-slice merge
+// (same result as spgemm_merge_symbolic) for callers that may not allocate
+// device memory and cannot hand the library a workspace -- for example code
+// that runs under a fixed device-memory budget reserved at start-up, or a
+// plug-in interface that passes only inputs and outputs.  Its scratch (the
+// device error word and the scan's per-tile partial sums) lives in one
+// file-scope device array of fixed size instead of a caller workspace, so the
+// call allocates nothing.
+//
+// Limits and sharing:
+// * at most kStaticMaxRows rows (2^24); larger inputs are rejected;
+// * every call on a device uses the same array, which keeps the last call's
+//   contents (the error word is cleared at the start of each call); calls
+//   that overlap on the GPU (other threads, other streams) race on it;
+// * the array's device address is looked up once per device, with that
+//   device current, by the first call made on it; make that first call
+//   before any stream capture.
+#include <cstdio>
+#include <mutex>
+
+#include "plan.h"
+
+namespace {
+
+constexpr long long kStaticMaxRows = 1LL << 24;
+constexpr size_t kCountersBytes = (sizeof(sg::DevCounters) + 255) / 256 * 256;
+constexpr size_t kPartialsBytes =
+    ((kStaticMaxRows + sg::kScanTile) / sg::kScanTile) * sizeof(int64_t);
+constexpr size_t kScratchBytes = kCountersBytes + (kPartialsBytes + 255) / 256 * 256;
+
+// Host code must not use this name as a device address: it is a host-side
+// stand-in.  The address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+spgemm_status static_fail(spgemm_status st, const char* msg) {
+    sg::set_last_error(msg);
+    return st;
+}
+
+// Device address of the scratch array on the current device (looked up once).
+cudaError_t scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
+                                           const spgemm_opts* opts, void* stream,
+                                           int64_t* rowptrC, int64_t* nnz_c) {
+    sg::set_last_error("");
+    if (c < 1 || c > 32 || !parts || !rowptrC || !nnz_c)
+        return static_fail(SPGEMM_ERR_INVALID_ARG, "need 1 <= c <= 32 parts and non-NULL outputs");
+    const long long m = parts[0].nrows, n = parts[0].ncols;
+    if (m < 0 || m > kStaticMaxRows)
+        return static_fail(SPGEMM_ERR_INVALID_ARG,
+                           "row count outside the static scratch limit (at most 16777216 rows)");
+    spgemm_opts o{};
+    if (opts) o = *opts;
+    const bool pattern = o.semiring == SPGEMM_OR_AND || parts[0].value_type == SPGEMM_BOOL;
+    for (int s = 0; s < c; ++s) {
+        const spgemm_csr& P = parts[s];
+        if (P.nrows != m || P.ncols != n || P.index_type != parts[0].index_type || !P.rowptr ||
+            (P.nnz > 0 && !P.col))
+            return static_fail(SPGEMM_ERR_INVALID_ARG, "parts differ in shape or index type, or miss arrays");
+    }
+    void* base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
+    unsigned char* w = (unsigned char*)base;
+    sg::DevCounters* cnt = (sg::DevCounters*)w;
+    int64_t* partials = (int64_t*)(w + kCountersBytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the error word must start at zero; the partials are overwritten
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(sg::DevCounters), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(rowptrC + m, 0, sizeof(int64_t), s)) != cudaSuccess)
+        return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
+    const int vt = pattern ? SPGEMM_BOOL : parts[0].value_type;
+    e = sg::launch_merge(c, parts, vt, m, n, sms, s, false, rowptrC, nullptr, nullptr, nullptr,
+                         &cnt->err);
+    if (e == cudaSuccess) e = sg::launch_exclusive_scan(rowptrC, m + 1, partials, s);
+    int64_t total = 0;
+    int herr = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, rowptrC + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&herr, &cnt->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
+    if (herr) return static_fail(SPGEMM_ERR_INTERNAL, "device check failed in the merge count");
+    *nnz_c = total;
+    return SPGEMM_OK;
+}
+
+}  // extern "C"

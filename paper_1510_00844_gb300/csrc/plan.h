@@ -45,6 +45,8 @@ namespace sg {
 
 // Process-wide count of kernels this library has launched.
 void count_launches(long long k);
+// Message returned by spgemm_last_error() on this thread.
+void set_last_error(const char* msg);
 
 struct WsLayout {
     size_t chunkcnt = 0, segtab = 0, runlen = 0, arena = 0, scan = 0, total = 0;

@@ -76,6 +76,7 @@ def _load():
         "spgemm_merge_symbolic": (st, [I32_, P, P, P, P, S, P, P]),
         "spgemm_merge_numeric": (st, [I32_, P, P, P, P, S, P, P, P]),
         "spgemm_merge_check": (st, [P, P]),
+        "spgemm_merge_symbolic_static": (st, [I32_, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -290,6 +291,23 @@ def merge_symbolic(parts: Sequence[DeviceCSR], ws: torch.Tensor, semiring: int =
     _check(_lib.spgemm_merge_symbolic(len(parts), arr, ctypes.byref(opts), _stream(stream),
                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                       ctypes.c_void_p(rowptrC.data_ptr()), ctypes.byref(nnz)))
+    return rowptrC, int(nnz.value)
+
+
+def merge_symbolic_static(parts: Sequence[DeviceCSR], semiring: int = PLUS_TIMES, stream=None,
+                          rowptrC: Optional[torch.Tensor] = None):
+    """spgemm_merge_symbolic_static: the merge count with no workspace (the
+    library's fixed device scratch array is used instead)."""
+    m = parts[0].nrows
+    if rowptrC is None:
+        rowptrC = torch.empty(m + 1, dtype=torch.int64, device=parts[0].rowptr.device)
+    arr = _parts(parts)
+    opts = _Opts(semiring, 0)
+    nnz = ctypes.c_int64()
+    _check(_lib.spgemm_merge_symbolic_static(len(parts), arr, ctypes.byref(opts),
+                                             _stream(stream),
+                                             ctypes.c_void_p(rowptrC.data_ptr()),
+                                             ctypes.byref(nnz)))
     return rowptrC, int(nnz.value)
 
 
