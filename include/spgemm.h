@@ -84,10 +84,14 @@ typedef struct {
 } spgemm_csr;
 
 typedef struct {
-    int32_t semiring;    /* spgemm_semiring; OR_AND ignores values and yields a pattern */
-    int32_t checked;     /* nonzero: validate A and B on the device before planning */
-    int32_t dense_chunk; /* columns per dense-row chunk: 0 = library choice, 1024 or 2048 */
-    int32_t reserved[5]; /* must be zero */
+    int32_t semiring;        /* spgemm_semiring; OR_AND ignores values and yields a pattern */
+    int32_t checked;         /* nonzero: validate A and B on the device before planning */
+    int32_t dense_chunk;     /* columns per dense-row chunk: 0 = library choice, 1024 or 2048 */
+    int32_t dense_min_flops; /* rows with more products use dense accumulators:
+                                0 = 1024, else 32..1024 (autotuned knob) */
+    int32_t max_row_nnz;     /* device-sized plans: bound on the entries of a dense row of A
+                                (cursor arena slot), 0 = 65536 */
+    int32_t reserved[3];     /* must be zero */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s* spgemm_plan_t;
@@ -133,6 +137,41 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
                           void* stream, void* plan_ws, size_t plan_ws_bytes,
                           spgemm_plan_t* plan);
 
+/* ---- batches of products (many independent C_p = A_p . B_p in one set of
+ *      launches) ----
+ * A batch plan numbers the rows of all products consecutively (product p owns
+ * rows [sum_{q<p} m_q, sum_{q<=p} m_q)); spgemm_symbolic / spgemm_numeric then
+ * produce the concatenation: rowptrC has (sum m_p)+1 entries, product p's
+ * entries are colC/valC[rowptrC[row_base_p] .. rowptrC[row_base_p + m_p]).
+ * All products share one index type and one value type.  Not in the paper;
+ * the paper's local multiply is one product per process (Alg. 2). */
+size_t spgemm_batch_plan_workspace_size(int32_t count, const spgemm_csr* A);
+spgemm_status spgemm_batch_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                                const spgemm_opts* opts, void* stream, void* plan_ws,
+                                size_t plan_ws_bytes, spgemm_plan_t* plan);
+
+/* Per-product row pointers of a batch result: out[row_base_p + p + i] =
+ * rowptrC[row_base_p + i] - rowptrC[row_base_p] for i = 0..m_p (each product's
+ * rowptr array, m_p + 1 entries, stored one after the other).  No wait. */
+spgemm_status spgemm_batch_rowptrs(spgemm_plan_t plan, const int64_t* rowptrC, int64_t* out);
+
+/* ---- device-sized plans: the whole product enqueued with no host readback,
+ *      so a sequence of products (e.g. the levels of an AMG hierarchy) can be
+ *      captured in a CUDA graph and replayed ----
+ * spgemm_plan_device records the batch and sizes every workspace by upper
+ * bounds (B's nnz fields are read as capacities; A rows longer than
+ * opts.max_row_nnz that need the dense path are reported by spgemm_check).
+ * It does no device work besides uploading the descriptors and waits for
+ * that upload.  spgemm_execute then enqueues row analysis, symbolic phase,
+ * scan and numeric phase; C goes to colC/valC (capacity entries); nnz(C) is
+ * rowptrC[sum m_p] on the device.  If C exceeds the capacity nothing beyond it
+ * is written and spgemm_check reports OUT_OF_MEMORY. */
+spgemm_status spgemm_plan_device(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                                 const spgemm_opts* opts, void* stream, void* plan_ws,
+                                 size_t plan_ws_bytes, spgemm_plan_t* plan);
+spgemm_status spgemm_execute(spgemm_plan_t plan, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                             int64_t capacity, void* colC, void* valC);
+
 /* Statistics of a plan (host call, no device work). */
 spgemm_status spgemm_plan_info(spgemm_plan_t plan, spgemm_info* info);
 
@@ -156,12 +195,24 @@ spgemm_status spgemm_numeric(spgemm_plan_t plan, void* ws, size_t ws_bytes,
                              const int64_t* rowptrC, void* colC, void* valC);
 
 /* Reads the plan's device error word (waits for the stream).  Returns
- * SPGEMM_ERR_INTERNAL if a device-side check failed since the plan was
- * made. */
+ * OUT_OF_MEMORY if C exceeded the capacity of spgemm_execute, NOT_SUPPORTED
+ * if a dense row exceeded max_row_nnz, INTERNAL if another device-side check
+ * failed since the plan was made. */
 spgemm_status spgemm_check(spgemm_plan_t plan);
 
 /* Release a plan (host memory only; the caller frees plan_ws). */
 void spgemm_plan_destroy(spgemm_plan_t plan);
+
+/* ---- transpose ----
+ * spgemm_transpose -- A^T (n x m) in CSR with ascending columns: rowptrT
+ * int64[n+1], colT (index type of A) and valT (value type of A; NULL for
+ * BOOL) of nnz(A) entries, all device, caller-owned.  `ws` is device memory of
+ * spgemm_transpose_workspace_size(A) bytes, 256-byte aligned.  Does not wait.
+ * The paper transposes the B blocks locally while redistributing them
+ * (Alg. 2, the all-to-all of B); here it provides R^T for R^T A R. */
+size_t spgemm_transpose_workspace_size(const spgemm_csr* A);
+spgemm_status spgemm_transpose(const spgemm_csr* A, void* stream, void* ws, size_t ws_bytes,
+                               int64_t* rowptrT, void* colT, void* valT);
 
 /* ---- k-slices and their merge (Alg. 2 split of the inner dimension;
  *      multiway merge with duplicate reduction, Sec. 4.3) ---- */

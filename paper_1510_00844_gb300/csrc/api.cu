@@ -83,70 +83,46 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 
 WsLayout workspace_layout(const Plan& P) {
     WsLayout L;
+    const bool dense = P.device_sized || P.ndense > 0;
     size_t off = 0;
     L.chunkcnt = off;
-    off += align_up((size_t)P.ndense * (size_t)P.P * sizeof(int32_t));
+    if (dense) off += align_up((size_t)P.chunk_total * sizeof(int32_t));
     L.segtab = off;
-    if (P.ndense > 0) off += align_up((size_t)P.l * (kSegGrid + 1) * sizeof(int32_t));
+    if (dense) off += align_up((size_t)P.seg_total * sizeof(int32_t));
     L.runlen = off;
-    if (P.ndense > 0) off += align_up((size_t)P.B.nnz * sizeof(int32_t));
+    if (dense) off += align_up((size_t)P.run_total * sizeof(int32_t));
     L.arena = off;
     L.arena_stride = std::max<long long>(1, P.max_dense_len);
-    if (P.ndense > 0)
+    if (dense)
         off += align_up((size_t)P.dense_grid * P.dense_warps_per_block * (size_t)L.arena_stride *
                         sizeof(DenseCursor));
     L.scan = off;
-    off += align_up(scan_temp_bytes(P.m + 1));
+    off += align_up(scan_temp_bytes(P.R + 1));
     L.total = off;
     return L;
 }
 
-// Units of the dense numeric phase: per flops class (floor(log2 flops) = lg),
-// G segments per row with about kSegFlops products per segment.
-void build_dense_units(Plan& P) {
-    constexpr long long kSegFlops = 1LL << 16;
-    DenseUnits& U = P.units;
-    int gmax = 1;
-    while (gmax * 2 <= std::min(kSegGrid, P.P)) gmax *= 2;
-    U.nclass = kMaxDenseClasses;
-    long long rb = 0, ub = 0;
-    for (int t = 0; t < kMaxDenseClasses; ++t) {
-        const int lg = kDenseMaxLog2 - t;
-        long long want = ((lg + 1 >= 62) ? (1LL << 62) : (1LL << (lg + 1))) / kSegFlops;
-        int G = 1;
-        while (G < gmax && G < want) G *= 2;
-        const long long cnt = (long long)P.class_count[kClassDense0 + t];
-        U.G[t] = G;
-        U.row_begin[t] = rb;
-        U.unit_begin[t] = ub;
-        rb += cnt;
-        ub += cnt * G;
-    }
-    U.unit_begin[kMaxDenseClasses] = ub;
+size_t plan_workspace_bytes(int nprod, long long R) {
+    if (R < 0) R = 0;
+    return align_up(sizeof(DevCounters)) + align_up((size_t)nprod * sizeof(ProdDesc)) +
+           2 * align_up((size_t)(nprod + 1) * sizeof(long long)) +
+           align_up((size_t)R * sizeof(int64_t)) + align_up((size_t)R) +
+           align_up((size_t)R * sizeof(int32_t));
 }
 
 }  // namespace sg
 
-extern "C" {
+namespace {
 
-int64_t spgemm_kernel_launches(void) { return sg::g_launches.load(); }
-
-const char* spgemm_version(void) { return "gb300-spgemm 0.1 (sm_103a)"; }
-
-const char* spgemm_last_error(void) { return g_last_error.c_str(); }
-
-size_t spgemm_plan_workspace_size(int64_t m) {
-    if (m < 0) m = 0;
-    return align_up(sizeof(sg::DevCounters)) + align_up((size_t)m * sizeof(int64_t)) +
-           align_up((size_t)m * sizeof(int32_t));
-}
-
-spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
-                          void* stream, void* plan_ws, size_t plan_ws_bytes,
-                          spgemm_plan_t* plan_out) {
+// Checks and records a batch of products; shared by spgemm_plan,
+// spgemm_batch_plan and spgemm_plan_device.
+spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                        const spgemm_opts* opts, void* stream, void* plan_ws, size_t plan_ws_bytes,
+                        bool device_sized, spgemm_plan_t* plan_out) {
     g_last_error.clear();
     if (!plan_out) return fail(SPGEMM_ERR_INVALID_ARG, "plan output pointer is NULL");
     *plan_out = nullptr;
+    if (count < 1) return fail(SPGEMM_ERR_INVALID_ARG, "a batch needs at least one product");
     spgemm_opts o{};
     if (opts) o = *opts;
     if (o.semiring != SPGEMM_PLUS_TIMES && o.semiring != SPGEMM_OR_AND)
@@ -154,22 +130,33 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
     if (o.dense_chunk != 0 && o.dense_chunk != sg::kDenseW0 && o.dense_chunk != sg::kDenseW1)
         return fail(SPGEMM_ERR_INVALID_ARG, "dense_chunk must be 0, %d or %d", sg::kDenseW0,
                     sg::kDenseW1);
+    if (o.dense_min_flops != 0 && (o.dense_min_flops < 32 || o.dense_min_flops > 1024))
+        return fail(SPGEMM_ERR_INVALID_ARG, "dense_min_flops must be 0 or in [32, 1024]");
+    if (o.max_row_nnz < 0) return fail(SPGEMM_ERR_INVALID_ARG, "max_row_nnz must be >= 0");
     if (!A || !B) return fail(SPGEMM_ERR_INVALID_ARG, "A or B is NULL");
-    const int vt = kernel_value_type(A, &o);
+    const int vt = kernel_value_type(&A[0], &o);
     const bool need_vals = vt != SPGEMM_BOOL;
-    spgemm_status st;
-    if ((st = check_csr(A, "A", need_vals)) != SPGEMM_OK) return st;
-    if ((st = check_csr(B, "B", need_vals)) != SPGEMM_OK) return st;
-    if (A->ncols != B->nrows)
-        return fail(SPGEMM_ERR_INVALID_ARG, "inner dimensions differ: A is %lld x %lld, B is %lld x %lld",
-                    (long long)A->nrows, (long long)A->ncols, (long long)B->nrows,
-                    (long long)B->ncols);
-    if (A->index_type != B->index_type)
-        return fail(SPGEMM_ERR_INVALID_ARG, "A and B index types differ");
-    if (need_vals && A->value_type != B->value_type)
-        return fail(SPGEMM_ERR_INVALID_ARG, "A and B value types differ");
-    if (B->rowend) return fail(SPGEMM_ERR_INVALID_ARG, "B must be a plain CSR (rowend NULL)");
-    const size_t need = spgemm_plan_workspace_size(A->nrows);
+    long long R = 0;
+    for (int p = 0; p < count; ++p) {
+        spgemm_status st;
+        if ((st = check_csr(&A[p], "A", need_vals)) != SPGEMM_OK) return st;
+        if ((st = check_csr(&B[p], "B", need_vals)) != SPGEMM_OK) return st;
+        if (A[p].ncols != B[p].nrows)
+            return fail(SPGEMM_ERR_INVALID_ARG,
+                        "product %d: inner dimensions differ: A is %lld x %lld, B is %lld x %lld", p,
+                        (long long)A[p].nrows, (long long)A[p].ncols, (long long)B[p].nrows,
+                        (long long)B[p].ncols);
+        if (A[p].index_type != A[0].index_type || B[p].index_type != A[0].index_type)
+            return fail(SPGEMM_ERR_INVALID_ARG, "product %d: index types differ", p);
+        if (need_vals && (A[p].value_type != A[0].value_type || B[p].value_type != A[0].value_type))
+            return fail(SPGEMM_ERR_INVALID_ARG, "product %d: value types differ", p);
+        if (B[p].rowend)
+            return fail(SPGEMM_ERR_INVALID_ARG, "product %d: B must be a plain CSR (rowend NULL)", p);
+        R += A[p].nrows;
+    }
+    if (R > 0x7fffffffLL)
+        return fail(SPGEMM_ERR_NOT_SUPPORTED, "a batch may have at most 2^31-1 rows in total");
+    const size_t need = sg::plan_workspace_bytes(count, R);
     if (!plan_ws || plan_ws_bytes < need)
         return fail(SPGEMM_ERR_OUT_OF_MEMORY, "plan workspace %zu bytes < %zu required",
                     plan_ws_bytes, need);
@@ -178,27 +165,21 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
 
     Plan* P = new (std::nothrow) Plan();
     if (!P) return fail(SPGEMM_ERR_OUT_OF_MEMORY, "host allocation of the plan failed");
-    P->A = *A;
-    P->B = *B;
+    auto bail = [&](spgemm_status s) {
+        delete P;
+        return s;
+    };
     P->opts = o;
     P->stream = (cudaStream_t)stream;
-    P->it = A->index_type;
+    P->it = A[0].index_type;
     P->vt = vt;
-    P->m = A->nrows;
-    P->l = A->ncols;
-    P->n = B->ncols;
+    P->nprod = count;
+    P->R = R;
+    P->device_sized = device_sized;
+    P->dense_min = o.dense_min_flops ? o.dense_min_flops : 1024;
     P->sm_count = device_sm_count(&P->smem_optin);
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
     P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;
-    P->pws = (unsigned char*)plan_ws;
-    P->pws_bytes = plan_ws_bytes;
-    size_t off = 0;
-    P->cnt = (sg::DevCounters*)(P->pws + off);
-    off += align_up(sizeof(sg::DevCounters));
-    P->flops = (int64_t*)(P->pws + off);
-    off += align_up((size_t)P->m * sizeof(int64_t));
-    P->rows = (int32_t*)(P->pws + off);
-    // dense chunk configuration: wider chunks for 8-byte values on larger n
     {
         const size_t vbytes = vt == SPGEMM_F64 || vt == SPGEMM_I64 ? 8 : vt == SPGEMM_F32 ? 4 : 0;
         int cfg = (vbytes == 8) ? 0 : 1;
@@ -206,32 +187,123 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
         if (o.dense_chunk == sg::kDenseW1) cfg = 1;
         P->W = cfg == 0 ? sg::kDenseW0 : sg::kDenseW1;
     }
-    P->P = (int)std::max<long long>(1, (P->n + P->W - 1) / P->W);
+    P->descs.resize(count);
+    std::vector<long long> rb(count + 1), bb(count + 1);
+    long long rbase = 0, bbase = 0, chunk = 0, seg = 0, run = 0;
+    for (int p = 0; p < count; ++p) {
+        sg::ProdDesc& d = P->descs[p];
+        d = sg::ProdDesc{};
+        d.m = A[p].nrows;
+        d.l = A[p].ncols;
+        d.n = B[p].ncols;
+        d.row_base = rbase;
+        d.brow_base = bbase;
+        d.rpA = A[p].rowptr;
+        d.reA = A[p].rowend;
+        d.ciA = A[p].col;
+        d.vA = need_vals ? A[p].val : nullptr;
+        d.rpB = B[p].rowptr;
+        d.ciB = B[p].col;
+        d.vB = need_vals ? B[p].val : nullptr;
+        d.nnzB = B[p].nnz;
+        d.P = (int)std::max<long long>(1, (d.n + P->W - 1) / P->W);
+        d.chunk_base = chunk;
+        d.seg_base = seg;
+        d.run_base = run;
+        rb[p] = rbase;
+        bb[p] = bbase;
+        rbase += d.m;
+        bbase += d.l;
+        chunk += d.m * d.P;
+        seg += d.l * (sg::kSegGrid + 1);
+        run += d.nnzB;
+        P->max_n = std::max(P->max_n, d.n);
+    }
+    rb[count] = rbase;
+    bb[count] = bbase;
+    P->LB = bbase;
+    P->chunk_total = chunk;
+    P->seg_total = seg;
+    P->run_total = run;
+    if (device_sized && P->max_n > P->max_dense_n)
+        return bail(fail(SPGEMM_ERR_NOT_SUPPORTED,
+                         "device-sized plans need n <= %lld columns in every product (n = %lld)",
+                         P->max_dense_n, P->max_n));
+    // plan workspace layout
+    P->pws = (unsigned char*)plan_ws;
+    P->pws_bytes = plan_ws_bytes;
+    size_t off = 0;
+    P->cnt = (sg::DevCounters*)(P->pws + off);
+    off += align_up(sizeof(sg::DevCounters));
+    P->d_descs = (sg::ProdDesc*)(P->pws + off);
+    off += align_up((size_t)count * sizeof(sg::ProdDesc));
+    P->rb = (long long*)(P->pws + off);
+    off += align_up((size_t)(count + 1) * sizeof(long long));
+    P->bb = (long long*)(P->pws + off);
+    off += align_up((size_t)(count + 1) * sizeof(long long));
+    P->flops = (int64_t*)(P->pws + off);
+    off += align_up((size_t)R * sizeof(int64_t));
+    P->cls = P->pws + off;
+    off += align_up((size_t)R);
+    P->rows = (int32_t*)(P->pws + off);
 
-    auto bail = [&](spgemm_status s) {
-        delete P;
-        return s;
-    };
     cudaStream_t s = P->stream;
-    cudaError_t e = cudaMemsetAsync(P->cnt, 0, sizeof(sg::DevCounters), s);
+    cudaError_t e = cudaMemcpyAsync(P->d_descs, P->descs.data(), count * sizeof(sg::ProdDesc),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->rb, rb.data(), (count + 1) * sizeof(long long),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->bb, bb.data(), (count + 1) * sizeof(long long),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: descriptor upload"));
+
+    auto prepare = [&]() -> cudaError_t {
+        const bool i32 = P->it == SPGEMM_INDEX_I32;
+        switch (P->vt) {
+            case SPGEMM_F64:
+                return i32 ? sg::prepare_numeric<int32_t, double>(*P) : sg::prepare_numeric<int64_t, double>(*P);
+            case SPGEMM_F32:
+                return i32 ? sg::prepare_numeric<int32_t, float>(*P) : sg::prepare_numeric<int64_t, float>(*P);
+            case SPGEMM_I64:
+                return i32 ? sg::prepare_numeric<int32_t, int64_t>(*P) : sg::prepare_numeric<int64_t, int64_t>(*P);
+            default:
+                return i32 ? sg::prepare_numeric<int32_t, sg::NoVal>(*P) : sg::prepare_numeric<int64_t, sg::NoVal>(*P);
+        }
+    };
+
+    if (device_sized) {
+        // sizes are upper bounds; the row analysis runs inside spgemm_execute
+        P->max_dense_len = o.max_row_nnz ? o.max_row_nnz : 65536;
+        e = prepare();
+        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: numeric setup"));
+        e = cudaStreamSynchronize(s);  // the descriptor upload reads host buffers
+        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: sync"));
+        *plan_out = P;
+        return SPGEMM_OK;
+    }
+
+    e = cudaMemsetAsync(P->cnt, 0, sizeof(sg::DevCounters), s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "plan: memset"));
     if (o.checked) {
         int* err = &P->cnt->err;
-        e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(*A, err, P->sm_count, s)
-                                      : sg::launch_validate<int64_t>(*A, err, P->sm_count, s);
-        if (e == cudaSuccess)
-            e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(*B, err, P->sm_count, s)
-                                          : sg::launch_validate<int64_t>(*B, err, P->sm_count, s);
+        for (int p = 0; p < count && e == cudaSuccess; ++p) {
+            e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(A[p], err, P->sm_count, s)
+                                          : sg::launch_validate<int64_t>(A[p], err, P->sm_count, s);
+            if (e == cudaSuccess)
+                e = P->it == SPGEMM_INDEX_I32 ? sg::launch_validate<int32_t>(B[p], err, P->sm_count, s)
+                                              : sg::launch_validate<int64_t>(B[p], err, P->sm_count, s);
+        }
         if (e != cudaSuccess) return bail(cuda_fail(e, "plan: validate"));
         int herr = 0;
         e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "plan: validate readback"));
         if (herr != 0)
-            return bail(fail(SPGEMM_ERR_INVALID_CSR,
-                             "invalid CSR input (%s)",
-                             herr == sg::kDevBadRowptr ? "row pointers not monotone or out of range"
-                                                       : "column index out of range, unsorted or duplicated"));
+            return bail(fail(SPGEMM_ERR_INVALID_CSR, "invalid CSR input (%s)",
+                             herr == sg::kDevBadRowptr
+                                 ? "row pointers not monotone or out of range"
+                                 : "column index out of range, unsorted or duplicated"));
     }
     e = P->it == SPGEMM_INDEX_I32 ? sg::launch_analyze<int32_t>(*P) : sg::launch_analyze<int64_t>(*P);
     if (e != cudaSuccess) return bail(cuda_fail(e, "plan: analyze"));
@@ -243,8 +315,8 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
     if (e != cudaSuccess) return bail(cuda_fail(e, "plan: readback"));
     if (h.unsupported)
         return bail(fail(SPGEMM_ERR_NOT_SUPPORTED,
-                         "rows with more than 1024 products need n <= %lld columns (n = %lld)",
-                         P->max_dense_n, P->n));
+                         "rows with more than %d products need n <= %lld columns (n = %lld)",
+                         P->dense_min, P->max_dense_n, P->max_n));
     long long acc = 0;
     for (int c = 0; c < sg::kNumClasses; ++c) {
         P->class_count[c] = h.class_count[c];
@@ -256,34 +328,82 @@ spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm
     P->max_flops = (long long)h.max_flops;
     P->ndense = acc - P->class_off[sg::kClassDense0];
     P->max_dense_len = (long long)h.max_dense_len;
-    sg::build_dense_units(*P);
-    {
-        const bool i32 = P->it == SPGEMM_INDEX_I32;
-        switch (P->vt) {
-            case SPGEMM_F64:
-                e = i32 ? sg::prepare_numeric<int32_t, double>(*P) : sg::prepare_numeric<int64_t, double>(*P);
-                break;
-            case SPGEMM_F32:
-                e = i32 ? sg::prepare_numeric<int32_t, float>(*P) : sg::prepare_numeric<int64_t, float>(*P);
-                break;
-            case SPGEMM_I64:
-                e = i32 ? sg::prepare_numeric<int32_t, int64_t>(*P) : sg::prepare_numeric<int64_t, int64_t>(*P);
-                break;
-            default:
-                e = i32 ? sg::prepare_numeric<int32_t, sg::NoVal>(*P) : sg::prepare_numeric<int64_t, sg::NoVal>(*P);
-                break;
-        }
-        if (e != cudaSuccess) return bail(cuda_fail(e, "plan: numeric setup"));
-    }
+    e = prepare();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan: numeric setup"));
     *plan_out = P;
     return SPGEMM_OK;
 }
 
+spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes) {
+    size_t need = sg::workspace_layout(*P).total;
+    if (need > 0 && (!ws || ws_bytes < need))
+        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "workspace %zu bytes < %zu required", ws_bytes, need);
+    if (ws && ((uintptr_t)ws) % kAlign)
+        return fail(SPGEMM_ERR_INVALID_ARG, "workspace not %zu-byte aligned", kAlign);
+    return SPGEMM_OK;
+}
+
+cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long long cap,
+                        void* colC, void* valC) {
+    const bool i32 = P->it == SPGEMM_INDEX_I32;
+    switch (P->vt) {
+        case SPGEMM_F64:
+            return i32 ? sg::launch_numeric<int32_t, double>(*P, w, rowptrC, cap, colC, valC)
+                       : sg::launch_numeric<int64_t, double>(*P, w, rowptrC, cap, colC, valC);
+        case SPGEMM_F32:
+            return i32 ? sg::launch_numeric<int32_t, float>(*P, w, rowptrC, cap, colC, valC)
+                       : sg::launch_numeric<int64_t, float>(*P, w, rowptrC, cap, colC, valC);
+        case SPGEMM_I64:
+            return i32 ? sg::launch_numeric<int32_t, int64_t>(*P, w, rowptrC, cap, colC, valC)
+                       : sg::launch_numeric<int64_t, int64_t>(*P, w, rowptrC, cap, colC, valC);
+        default:
+            return i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, w, rowptrC, cap, colC, nullptr)
+                       : sg::launch_numeric<int64_t, sg::NoVal>(*P, w, rowptrC, cap, colC, nullptr);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t spgemm_kernel_launches(void) { return sg::g_launches.load(); }
+
+const char* spgemm_version(void) { return "gb300-spgemm 0.2 (sm_103a)"; }
+
+const char* spgemm_last_error(void) { return g_last_error.c_str(); }
+
+size_t spgemm_plan_workspace_size(int64_t m) { return sg::plan_workspace_bytes(1, m); }
+
+size_t spgemm_batch_plan_workspace_size(int32_t count, const spgemm_csr* A) {
+    long long R = 0;
+    if (A)
+        for (int p = 0; p < count; ++p) R += std::max<long long>(0, A[p].nrows);
+    return sg::plan_workspace_bytes(std::max(count, 1), R);
+}
+
+spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                          void* stream, void* plan_ws, size_t plan_ws_bytes,
+                          spgemm_plan_t* plan_out) {
+    return make_plan(1, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out);
+}
+
+spgemm_status spgemm_batch_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                                const spgemm_opts* opts, void* stream, void* plan_ws,
+                                size_t plan_ws_bytes, spgemm_plan_t* plan_out) {
+    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out);
+}
+
+spgemm_status spgemm_plan_device(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                                 const spgemm_opts* opts, void* stream, void* plan_ws,
+                                 size_t plan_ws_bytes, spgemm_plan_t* plan_out) {
+    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, true, plan_out);
+}
+
 spgemm_status spgemm_plan_info(spgemm_plan_t P, spgemm_info* info) {
     if (!P || !info) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
-    info->m = P->m;
-    info->l = P->l;
-    info->n = P->n;
+    info->m = P->R;
+    info->l = P->nprod == 1 ? P->descs[0].l : P->LB;
+    info->n = P->max_n;
     info->flops = P->total_flops;
     info->max_row_flops = P->max_flops;
     info->rows_empty = (int64_t)P->class_count[sg::kClassEmpty];
@@ -292,7 +412,7 @@ spgemm_status spgemm_plan_info(spgemm_plan_t P, spgemm_info* info) {
     info->rows_hash = h;
     info->rows_dense = P->ndense;
     info->chunk_width = P->W;
-    info->chunks_per_row = P->P;
+    info->chunks_per_row = P->nprod == 1 ? P->descs[0].P : 0;
     info->nnz_c = P->nnz_c;
     return SPGEMM_OK;
 }
@@ -303,33 +423,26 @@ spgemm_status spgemm_workspace_size(spgemm_plan_t P, size_t* bytes) {
     return SPGEMM_OK;
 }
 
-static spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes) {
-    size_t need = sg::workspace_layout(*P).total;
-    if (need > 0 && (!ws || ws_bytes < need))
-        return fail(SPGEMM_ERR_OUT_OF_MEMORY, "workspace %zu bytes < %zu required", ws_bytes, need);
-    if (ws && ((uintptr_t)ws) % kAlign)
-        return fail(SPGEMM_ERR_INVALID_ARG, "workspace not %zu-byte aligned", kAlign);
-    return SPGEMM_OK;
-}
-
 spgemm_status spgemm_symbolic(spgemm_plan_t P, void* ws, size_t ws_bytes, int64_t* rowptrC,
                               int64_t* nnz_c) {
     g_last_error.clear();
     if (!P || !rowptrC || !nnz_c) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    if (P->device_sized)
+        return fail(SPGEMM_ERR_INVALID_ARG, "device-sized plans run through spgemm_execute");
     spgemm_status st = check_ws(P, ws, ws_bytes);
     if (st != SPGEMM_OK) return st;
     cudaStream_t s = P->stream;
     unsigned char* w = (unsigned char*)ws;
-    SG_CUDA(cudaMemsetAsync(rowptrC + P->m, 0, sizeof(int64_t), s), "symbolic: memset");
+    SG_CUDA(cudaMemsetAsync(rowptrC + P->R, 0, sizeof(int64_t), s), "symbolic: memset");
     cudaError_t e = P->it == SPGEMM_INDEX_I32 ? sg::launch_symbolic<int32_t>(*P, w, rowptrC)
                                               : sg::launch_symbolic<int64_t>(*P, w, rowptrC);
     if (e != cudaSuccess) return cuda_fail(e, "symbolic");
     sg::WsLayout L = sg::workspace_layout(*P);
-    e = sg::launch_exclusive_scan(rowptrC, P->m + 1, (int64_t*)(w + L.scan), s);
+    e = sg::launch_exclusive_scan(rowptrC, P->R + 1, (int64_t*)(w + L.scan), s);
     if (e != cudaSuccess) return cuda_fail(e, "symbolic: scan");
     int64_t total = 0;
     int herr = 0;
-    SG_CUDA(cudaMemcpyAsync(&total, rowptrC + P->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+    SG_CUDA(cudaMemcpyAsync(&total, rowptrC + P->R, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
             "symbolic: readback");
     SG_CUDA(cudaMemcpyAsync(&herr, &P->cnt->err, sizeof(int), cudaMemcpyDeviceToHost, s),
             "symbolic: readback");
@@ -344,34 +457,51 @@ spgemm_status spgemm_numeric(spgemm_plan_t P, void* ws, size_t ws_bytes, const i
                              void* colC, void* valC) {
     g_last_error.clear();
     if (!P || !rowptrC) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    if (P->device_sized)
+        return fail(SPGEMM_ERR_INVALID_ARG, "device-sized plans run through spgemm_execute");
     if (P->nnz_c < 0) return fail(SPGEMM_ERR_INVALID_ARG, "spgemm_symbolic has not run on this plan");
     if (P->nnz_c > 0 && !colC) return fail(SPGEMM_ERR_INVALID_ARG, "colC is NULL");
     if (P->nnz_c > 0 && P->vt != SPGEMM_BOOL && !valC)
         return fail(SPGEMM_ERR_INVALID_ARG, "valC is NULL");
     spgemm_status st = check_ws(P, ws, ws_bytes);
     if (st != SPGEMM_OK) return st;
-    unsigned char* w = (unsigned char*)ws;
-    cudaError_t e = cudaSuccess;
-    const bool i32 = P->it == SPGEMM_INDEX_I32;
-    switch (P->vt) {
-        case SPGEMM_F64:
-            e = i32 ? sg::launch_numeric<int32_t, double>(*P, w, rowptrC, colC, valC)
-                    : sg::launch_numeric<int64_t, double>(*P, w, rowptrC, colC, valC);
-            break;
-        case SPGEMM_F32:
-            e = i32 ? sg::launch_numeric<int32_t, float>(*P, w, rowptrC, colC, valC)
-                    : sg::launch_numeric<int64_t, float>(*P, w, rowptrC, colC, valC);
-            break;
-        case SPGEMM_I64:
-            e = i32 ? sg::launch_numeric<int32_t, int64_t>(*P, w, rowptrC, colC, valC)
-                    : sg::launch_numeric<int64_t, int64_t>(*P, w, rowptrC, colC, valC);
-            break;
-        default:
-            e = i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, w, rowptrC, colC, nullptr)
-                    : sg::launch_numeric<int64_t, sg::NoVal>(*P, w, rowptrC, colC, nullptr);
-            break;
-    }
+    cudaError_t e = run_numeric(P, (unsigned char*)ws, rowptrC, P->nnz_c, colC, valC);
     if (e != cudaSuccess) return cuda_fail(e, "numeric");
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_execute(spgemm_plan_t P, void* ws, size_t ws_bytes, int64_t* rowptrC,
+                             int64_t capacity, void* colC, void* valC) {
+    g_last_error.clear();
+    if (!P || !rowptrC) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    if (!P->device_sized)
+        return fail(SPGEMM_ERR_INVALID_ARG, "spgemm_execute needs a plan from spgemm_plan_device");
+    if (capacity < 0) return fail(SPGEMM_ERR_INVALID_ARG, "negative capacity");
+    if (capacity > 0 && !colC) return fail(SPGEMM_ERR_INVALID_ARG, "colC is NULL");
+    if (capacity > 0 && P->vt != SPGEMM_BOOL && !valC)
+        return fail(SPGEMM_ERR_INVALID_ARG, "valC is NULL");
+    spgemm_status st = check_ws(P, ws, ws_bytes);
+    if (st != SPGEMM_OK) return st;
+    cudaStream_t s = P->stream;
+    unsigned char* w = (unsigned char*)ws;
+    SG_CUDA(cudaMemsetAsync(P->cnt, 0, sizeof(sg::DevCounters), s), "execute: memset");
+    cudaError_t e = P->it == SPGEMM_INDEX_I32 ? sg::launch_analyze<int32_t>(*P) : sg::launch_analyze<int64_t>(*P);
+    if (e == cudaSuccess) e = sg::launch_binning(*P);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rowptrC + P->R, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess)
+        e = P->it == SPGEMM_INDEX_I32 ? sg::launch_symbolic<int32_t>(*P, w, rowptrC)
+                                      : sg::launch_symbolic<int64_t>(*P, w, rowptrC);
+    sg::WsLayout L = sg::workspace_layout(*P);
+    if (e == cudaSuccess) e = sg::launch_exclusive_scan(rowptrC, P->R + 1, (int64_t*)(w + L.scan), s);
+    if (e == cudaSuccess) e = run_numeric(P, w, rowptrC, capacity, colC, valC);
+    if (e != cudaSuccess) return cuda_fail(e, "execute");
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_rowptrs(spgemm_plan_t P, const int64_t* rowptrC, int64_t* out) {
+    if (!P || !rowptrC || !out) return fail(SPGEMM_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = sg::launch_product_rowptr(*P, rowptrC, out);
+    if (e != cudaSuccess) return cuda_fail(e, "batch rowptrs");
     return SPGEMM_OK;
 }
 
@@ -381,6 +511,9 @@ spgemm_status spgemm_check(spgemm_plan_t P) {
     SG_CUDA(cudaMemcpyAsync(&herr, &P->cnt->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream),
             "check: readback");
     SG_CUDA(cudaStreamSynchronize(P->stream), "check: sync");
+    if (herr == sg::kDevCapacity) return fail(SPGEMM_ERR_OUT_OF_MEMORY, "C did not fit the output capacity");
+    if (herr == sg::kDevArena)
+        return fail(SPGEMM_ERR_NOT_SUPPORTED, "a dense row of A is longer than max_row_nnz");
     if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed (code %d)", herr);
     return SPGEMM_OK;
 }

@@ -4,25 +4,32 @@
 
 namespace sg {
 
-// Class offsets (exclusive scan of the counts), one thread.
+// Class offsets (exclusive scan of the counts) and the dense work-unit
+// prefix, one thread.
 __global__ void class_offsets_kernel(DevCounters* cnt) {
     unsigned long long s = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         cnt->class_cursor[c] = s;
+        cnt->class_off[c] = s;
         s += cnt->class_count[c];
     }
+    cnt->class_off[kNumClasses] = s;
+    unsigned long long u = 0;
+    for (int t = 0; t < kMaxDenseClasses; ++t) {
+        cnt->unit_begin[t] = u;
+        u += cnt->class_count[kClassDense0 + t] * (unsigned long long)dense_class_segments(t);
+    }
+    cnt->unit_begin[kMaxDenseClasses] = u;
 }
 
-// Scatter row ids into their class segment (order inside a class is free;
-// rows are independent).
-__global__ void bin_rows_kernel(long long m, long long n, long long max_dense_n,
-                                const int64_t* __restrict__ flops, int32_t* __restrict__ rows,
-                                DevCounters* cnt) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (long long)gridDim.x * blockDim.x) {
-        int c = row_class(flops[i], n, max_dense_n, nullptr);
-        unsigned long long pos = atomicAdd(&cnt->class_cursor[c], 1ull);
-        rows[pos] = (int32_t)i;
+// Scatter global row ids into their class segment (order inside a class is
+// free; rows are independent).
+__global__ void bin_rows_kernel(long long R, const unsigned char* __restrict__ cls,
+                                int32_t* __restrict__ rows, DevCounters* cnt) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+         r += (long long)gridDim.x * blockDim.x) {
+        unsigned long long pos = atomicAdd(&cnt->class_cursor[cls[r]], 1ull);
+        rows[pos] = (int32_t)r;
     }
 }
 
@@ -102,22 +109,40 @@ __global__ void scan_apply_kernel(int64_t* __restrict__ x, long long N,
 }
 
 // Empty rows: count 0.
-__global__ void zero_rows_kernel(const int32_t* __restrict__ rows, long long nrows,
+__global__ void zero_rows_kernel(const int32_t* __restrict__ rows, const DevCounters* cnt,
                                  int64_t* __restrict__ rowcnt) {
+    const long long nrows = (long long)cnt->class_count[kClassEmpty];
+    const int32_t* erow = rows + cnt->class_off[kClassEmpty];
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
          r += (long long)gridDim.x * blockDim.x)
-        rowcnt[rows[r]] = 0;
+        rowcnt[erow[r]] = 0;
 }
 
+// Relative row pointers of every product: out[out_base_p + i] = g[rb_p + i] - g[rb_p].
+__global__ void product_rowptr_kernel(long long R, const long long* __restrict__ rb, int nprod,
+                                      const int64_t* __restrict__ g, int64_t* __restrict__ out) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < R + nprod;
+         t += (long long)gridDim.x * blockDim.x) {
+        // entry t belongs to product p with rb[p] + p <= t < rb[p+1] + p + 1
+        int lo = 0, hi = nprod - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (rb[mid] + mid <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const long long i = t - rb[lo] - lo;
+        out[t] = g[rb[lo] + i] - g[rb[lo]];
+    }
+}
 
 cudaError_t launch_binning(Plan& P) {
-    const long long m = P.m;
+    const long long R = P.R;
     count_launches(1);
     class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt);
-    if (m > 0) {
-        int blocks = (int)std::min<long long>((m + 255) / 256, (long long)P.sm_count * 8);
+    if (R > 0) {
+        int blocks = (int)std::min<long long>((R + 255) / 256, (long long)P.sm_count * 8);
         count_launches(1);
-        bin_rows_kernel<<<blocks, 256, 0, P.stream>>>(m, P.n, P.max_dense_n, P.flops, P.rows, P.cnt);
+        bin_rows_kernel<<<blocks, 256, 0, P.stream>>>(R, P.cls, P.rows, P.cnt);
     }
     return cudaGetLastError();
 }
@@ -139,12 +164,18 @@ cudaError_t launch_exclusive_scan(int64_t* x, long long N, int64_t* temp, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_rows(const int32_t* rows, long long nrows, int64_t* rowcnt, int sm_count,
-                             cudaStream_t s) {
-    if (nrows <= 0) return cudaSuccess;
-    int blocks = (int)std::min<long long>((nrows + 255) / 256, (long long)sm_count * 8);
+cudaError_t launch_zero_rows(const Plan& P, int64_t* rowcnt) {
+    int blocks = P.sm_count * 4;
     count_launches(1);
-    zero_rows_kernel<<<blocks, 256, 0, s>>>(rows, nrows, rowcnt);
+    zero_rows_kernel<<<blocks, 256, 0, P.stream>>>(P.rows, P.cnt, rowcnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_product_rowptr(const Plan& P, const int64_t* g, int64_t* out) {
+    const long long total = P.R + P.nprod;
+    int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, (long long)P.sm_count * 8));
+    count_launches(1);
+    product_rowptr_kernel<<<blocks, 256, 0, P.stream>>>(P.R, P.rb, P.nprod, g, out);
     return cudaGetLastError();
 }
 

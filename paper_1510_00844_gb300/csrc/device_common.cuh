@@ -18,6 +18,8 @@ enum DevErr : int {
     kDevCountMismatch = 2,
     kDevBadIndex = 3,    // checked mode: column out of range / unsorted
     kDevBadRowptr = 4,
+    kDevCapacity = 5,    // C did not fit the output capacity
+    kDevArena = 6,       // a dense row is longer than the cursor arena slot
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

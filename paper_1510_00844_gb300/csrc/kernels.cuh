@@ -29,10 +29,41 @@ constexpr int kClassEmpty = 0;
 constexpr int kClassHash0 = 1;
 constexpr int kClassDense0 = kClassHash0 + kNumHashBins;          // largest-flops bucket
 constexpr int kNumClasses = kClassDense0 + (kDenseMaxLog2 - kDenseMinLog2 + 1);
+constexpr int kSegGrid = 16;
+// Dense chunk configurations (columns per chunk, warps per block): one is
+// chosen per plan (spgemm_opts.reserved[0] = 1 or 2 forces one).
+constexpr int kDenseW0 = 1024, kDenseWarps0 = 8;
+constexpr int kDenseW1 = 2048, kDenseWarps1 = 4;
+
+// One product of a batch (C_p = A_p . B_p).  Rows of all products are
+// numbered globally: product p owns global rows [row_base, row_base + m) and
+// global B rows [brow_base, brow_base + l).  The workspace offsets give each
+// product its slice of the shared tables.
+struct ProdDesc {
+    long long m, l, n;
+    long long row_base, brow_base;
+    const int64_t* rpA;
+    const int64_t* reA;
+    const void* ciA;
+    const void* vA;
+    const int64_t* rpB;
+    const void* ciB;
+    const void* vB;
+    long long nnzB;
+    long long chunk_base;  // dense chunk counts: chunk_base + i * P + c
+    long long seg_base;    // segment table: seg_base + k * (kSegGrid + 1) + g
+    long long run_base;    // run lengths: run_base + q (q a position in B's arrays)
+    int P;                 // column chunks per row
+    int pad;
+};
+
+constexpr int kMaxDenseClasses = kDenseMaxLog2 - kDenseMinLog2 + 1;
 
 struct DevCounters {
     unsigned long long class_count[kNumClasses];
     unsigned long long class_cursor[kNumClasses];
+    unsigned long long class_off[kNumClasses + 1];
+    unsigned long long unit_begin[kMaxDenseClasses + 1];  // dense work units per class
     unsigned long long total_flops;
     unsigned long long max_flops;
     unsigned long long work_counter[4];  // dynamic row grabbing
@@ -42,25 +73,86 @@ struct DevCounters {
     int pad[30];
 };
 
+// Product owning global row r: the largest p with rb[p] <= r.
+__device__ __forceinline__ int find_prod(const long long* __restrict__ rb, int nprod, long long r) {
+    int lo = 0, hi = nprod - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (rb[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Everything a kernel needs about global row r.
+template <class IT, class V>
+struct RowCtx {
+    long long i, a0, a1, n;
+    const IT* ciA;
+    const V* vA;
+    const int64_t* rpB;
+    const IT* ciB;
+    const V* vB;
+    long long chunk_base, seg_base, run_base;
+    int P;
+};
+
+template <class IT, class V>
+__device__ __forceinline__ RowCtx<IT, V> row_ctx(const ProdDesc* __restrict__ D,
+                                                 const long long* __restrict__ rb, int nprod,
+                                                 long long r) {
+    const int p = nprod > 1 ? find_prod(rb, nprod, r) : 0;
+    const ProdDesc& d = D[p];
+    RowCtx<IT, V> c;
+    c.i = r - d.row_base;
+    c.a0 = d.rpA[c.i];
+    c.a1 = d.reA ? d.reA[c.i] : d.rpA[c.i + 1];
+    c.n = d.n;
+    c.ciA = (const IT*)d.ciA;
+    c.vA = (const V*)d.vA;
+    c.rpB = d.rpB;
+    c.ciB = (const IT*)d.ciB;
+    c.vB = (const V*)d.vB;
+    c.chunk_base = d.chunk_base;
+    c.seg_base = d.seg_base;
+    c.run_base = d.run_base;
+    c.P = d.P;
+    return c;
+}
+
 // Tile of the int64 exclusive scan: 256 threads x 16 items.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__host__ __device__ __forceinline__ int row_class(long long flops, long long n, long long max_dense_n,
-                                                   int* unsupported) {
+// Class of a row with `flops` products: EMPTY, the smallest hash bin that
+// holds it while flops <= dense_min (<= 1024), else the dense bucket of
+// floor(log2 flops), largest first.
+__host__ __device__ __forceinline__ int row_class(long long flops, int dense_min) {
     if (flops == 0) return kClassEmpty;
+    if (flops <= dense_min) {
 #pragma unroll
-    for (int b = 0; b < kNumHashBins; ++b)
-        if (flops <= hash_bin_flops(b)) return kClassHash0 + b;
-    if (n > max_dense_n && unsupported) *unsupported = 1;
+        for (int b = 0; b < kNumHashBins; ++b)
+            if (flops <= hash_bin_flops(b)) return kClassHash0 + b;
+    }
 #ifdef __CUDA_ARCH__
     int lg = 63 - __clzll(flops);
 #else
     int lg = 63 - __builtin_clzll((unsigned long long)flops);
 #endif
     if (lg > kDenseMaxLog2) lg = kDenseMaxLog2;
+    if (lg < kDenseMinLog2) lg = kDenseMinLog2;
     return kClassDense0 + (kDenseMaxLog2 - lg);
+}
+
+// Segments per row of dense class t (floor(log2 flops) = kDenseMaxLog2 - t):
+// about 2^16 products per segment, at most kSegGrid.
+__host__ __device__ __forceinline__ int dense_class_segments(int t) {
+    const int lg = kDenseMaxLog2 - t;
+    int sh = lg + 1 - 16;
+    if (sh < 0) sh = 0;
+    if (sh > 4) sh = 4;  // kSegGrid = 16
+    return 1 << sh;
 }
 
 __device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* re, long long i) {
@@ -68,12 +160,14 @@ __device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* r
 }
 
 // ----------------------------------------------------------------- K1: flops
-// One warp per row: flops_i, its class, per-class counts, total and max.
+// One warp per global row: flops_i, its class, per-class counts, total and
+// max flops, longest dense row; a product whose dense rows need more columns
+// than the shared-memory bitmap holds is flagged.
 template <class IT>
-__global__ void analyze_kernel(long long m, long long n, long long max_dense_n,
-                               const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
-                               const IT* __restrict__ ciA, const int64_t* __restrict__ rpB,
-                               int64_t* __restrict__ flops_out, DevCounters* cnt) {
+__global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
+                               const long long* __restrict__ rb, int nprod, long long max_dense_n,
+                               int dense_min, int64_t* __restrict__ flops_out,
+                               unsigned char* __restrict__ cls_out, DevCounters* cnt) {
     __shared__ unsigned long long hist[kNumClasses];
     __shared__ unsigned long long blk_total, blk_max, blk_dlen;
     __shared__ int blk_unsup;
@@ -89,21 +183,23 @@ __global__ void analyze_kernel(long long m, long long n, long long max_dense_n,
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_total = 0, my_max = 0;
-    for (long long i = warp; i < m; i += nwarps) {
-        long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+    for (long long r = warp; r < R; r += nwarps) {
+        const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
         long long f = 0;
-        for (long long p = a0 + lane; p < a1; p += 32) {
-            long long k = (long long)ciA[p];
-            f += rpB[k + 1] - rpB[k];
+        for (long long p = c.a0 + lane; p < c.a1; p += 32) {
+            long long k = (long long)c.ciA[p];
+            f += c.rpB[k + 1] - c.rpB[k];
         }
         f = warp_sum(f);
         if (lane == 0) {
-            flops_out[i] = f;
-            int uns = 0;
-            int c = row_class(f, n, max_dense_n, &uns);
-            if (uns) blk_unsup = 1;
-            atomicAdd(&hist[c], 1ull);
-            if (c >= kClassDense0) atomicMax(&blk_dlen, (unsigned long long)(a1 - a0));
+            flops_out[r] = f;
+            const int cl = row_class(f, dense_min);
+            cls_out[r] = (unsigned char)cl;
+            if (cl >= kClassDense0) {
+                if (c.n > max_dense_n) blk_unsup = 1;
+                atomicMax(&blk_dlen, (unsigned long long)(c.a1 - c.a0));
+            }
+            atomicAdd(&hist[cl], 1ull);
             my_total += (unsigned long long)f;
             if ((unsigned long long)f > my_max) my_max = (unsigned long long)f;
         }
@@ -149,10 +245,9 @@ __global__ void validate_kernel(long long m, long long ncols, long long nnz, con
 // One warp per row; table of 2^LOG2T keys per warp.  Row count -> rowcnt[i].
 template <class IT, int LOG2T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-    symbolic_hash_kernel(const int32_t* __restrict__ rows, long long nrows,
-                         const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
-                         const IT* __restrict__ ciA, const int64_t* __restrict__ rpB,
-                         const IT* __restrict__ ciB, int64_t* __restrict__ rowcnt, int* err) {
+    symbolic_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
+                         int cls, int64_t* __restrict__ rowcnt, int* err) {
     using K = typename KeyT<IT>::type;
     constexpr int T = 1 << LOG2T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,11 +256,17 @@ __global__ void __launch_bounds__(WARPS * 32)
     K* keys = reinterpret_cast<K*>(smem_raw) + (size_t)w * T;
     for (int s = lane; s < T; s += 32) keys[s] = K(-1);
     __syncwarp();
+    const long long nrows = (long long)cnt->class_count[cls];
+    const int32_t* crow = rows + cnt->class_off[cls];
     const long long gw = (long long)blockIdx.x * WARPS + w;
     const long long nw = (long long)gridDim.x * WARPS;
-    for (long long r = gw; r < nrows; r += nw) {
-        const long long i = rows[r];
-        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+    for (long long rr = gw; rr < nrows; rr += nw) {
+        const long long r = crow[rr];
+        const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
+        const long long a0 = c.a0, a1 = c.a1;
+        const IT* ciA = c.ciA;
+        const int64_t* rpB = c.rpB;
+        const IT* ciB = c.ciB;
         int count = 0;
         for (long long b = a0; b < a1; b += 32) {
             const int nb = (int)min(32LL, a1 - b);
@@ -189,41 +290,50 @@ __global__ void __launch_bounds__(WARPS * 32)
                 }
             });
         }
-        if (lane == 0) rowcnt[i] = count;
+        if (lane == 0) rowcnt[r] = count;
         for (int s = lane; s < T; s += 32) keys[s] = K(-1);
         __syncwarp();
     }
 }
 
 // -------------------------------------------------- symbolic: dense rows
-// One block per row (dynamic row grabbing), bitmap of all n columns in shared
-// memory.  Also writes the per-chunk counts chunkcnt[r*P + c] (chunk c covers
-// columns [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
+// One block per row (dynamic row grabbing), bitmap of the product's n columns
+// in shared memory (sized for the largest n of the batch).  Also writes the
+// per-chunk counts chunkcnt[chunk_base + i*P + c] (chunk c covers columns
+// [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
 template <class IT>
-__global__ void symbolic_dense_kernel(const int32_t* __restrict__ rows, long long nrows,
-                                      const int64_t* __restrict__ rpA,
-                                      const int64_t* __restrict__ reA, const IT* __restrict__ ciA,
-                                      const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
-                                      long long n, int chunk_words, int P,
+__global__ void symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+                                      const long long* __restrict__ rb, int nprod,
+                                      const int32_t* __restrict__ rows, const DevCounters* cnt,
+                                      int max_words, int chunk_words,
                                       int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
                                       unsigned long long* work) {
     extern __shared__ unsigned bm[];
     __shared__ long long row_total;
     __shared__ long long cur_row;
-    const int NW = (int)((n + 31) >> 5);
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    for (int t = threadIdx.x; t < NW; t += blockDim.x) bm[t] = 0u;
+    unsigned long long nd = 0;
+    for (int t = kClassDense0; t < kNumClasses; ++t) nd += cnt->class_count[t];
+    const long long nrows = (long long)nd;
+    const int32_t* drow = rows + cnt->class_off[kClassDense0];
+    for (int t = threadIdx.x; t < max_words; t += blockDim.x) bm[t] = 0u;
     if (threadIdx.x == 0) row_total = 0;
     __syncthreads();
     while (true) {
         if (threadIdx.x == 0) cur_row = (long long)atomicAdd(work, 1ull);
         __syncthreads();
-        const long long r = cur_row;
-        if (r >= nrows) break;
-        const long long i = rows[r];
-        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        const long long rr = cur_row;
+        if (rr >= nrows) break;
+        const long long r = drow[rr];
+        const RowCtx<IT, NoVal> cx = row_ctx<IT, NoVal>(D, rb, nprod, r);
+        const long long a0 = cx.a0, a1 = cx.a1;
+        const IT* ciA = cx.ciA;
+        const int64_t* rpB = cx.rpB;
+        const IT* ciB = cx.ciB;
+        const int NW = (int)((cx.n + 31) >> 5);
+        const int P = cx.P;
         for (long long b = a0 + (long long)w * 32; b < a1; b += (long long)nwarps * 32) {
             const int nb = (int)min(32LL, a1 - b);
             long long lo = 0;
@@ -254,13 +364,13 @@ __global__ void symbolic_dense_kernel(const int32_t* __restrict__ rows, long lon
                 bm[t] = 0u;
             }
             s = warp_sum(s);
-            if (lane == 0) chunkcnt[r * P + c] = s;
+            if (lane == 0) chunkcnt[cx.chunk_base + cx.i * P + c] = s;
             part += s;
         }
         if (lane == 0 && part) atomicAdd((unsigned long long*)&row_total, (unsigned long long)part);
         __syncthreads();
         if (threadIdx.x == 0) {
-            rowcnt[i] = row_total;
+            rowcnt[r] = row_total;
             row_total = 0;
         }
         __syncthreads();
@@ -298,11 +408,9 @@ __device__ __forceinline__ void warp_bitonic_sort(K* keys, V* vals, int N) {
 // ascending k (ordered rounds); table compacted, sorted, written.
 template <class IT, class V, int LOG2T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-    numeric_hash_kernel(const int32_t* __restrict__ rows, long long nrows,
-                        const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
-                        const IT* __restrict__ ciA, const V* __restrict__ vA,
-                        const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
-                        const V* __restrict__ vB, const int64_t* __restrict__ rpC,
+    numeric_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                        int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
+                        int cls, const int64_t* __restrict__ rpC, long long cap,
                         IT* __restrict__ ciC, V* __restrict__ vC, int* err) {
     using K = typename KeyT<IT>::type;
     constexpr int T = 1 << LOG2T;
@@ -320,11 +428,19 @@ __global__ void __launch_bounds__(WARPS * 32)
         if constexpr (HV) acc[s] = VOps<V>::init();
     }
     __syncwarp();
+    const long long nrows = (long long)cnt->class_count[cls];
+    const int32_t* crow = rows + cnt->class_off[cls];
     const long long gw = (long long)blockIdx.x * WARPS + w;
     const long long nw = (long long)gridDim.x * WARPS;
-    for (long long r = gw; r < nrows; r += nw) {
-        const long long i = rows[r];
-        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+    for (long long rr = gw; rr < nrows; rr += nw) {
+        const long long r = crow[rr];
+        const RowCtx<IT, V> c = row_ctx<IT, V>(D, rb, nprod, r);
+        const long long a0 = c.a0, a1 = c.a1;
+        const IT* ciA = c.ciA;
+        const V* vA = c.vA;
+        const int64_t* rpB = c.rpB;
+        const IT* ciB = c.ciB;
+        const V* vB = c.vB;
         for (long long b = a0; b < a1; b += 32) {
             const int nb = (int)min(32LL, a1 - b);
             long long lo = 0;
@@ -351,8 +467,8 @@ __global__ void __launch_bounds__(WARPS * 32)
             });
         }
         // compact occupied slots to the front (ascending slot order)
-        const long long out = rpC[i];
-        const int cnt = (int)(rpC[i + 1] - out);
+        const long long out = rpC[r];
+        const int rcnt = (int)(rpC[r + 1] - out);
         int pos = 0;
         for (int s0 = 0; s0 < T; s0 += 32) {
             K kk = keys[s0 + lane];
@@ -369,14 +485,15 @@ __global__ void __launch_bounds__(WARPS * 32)
             pos += __popc(msk);
             __syncwarp();
         }
-        if (pos != cnt && lane == 0) atomicExch(err, (int)kDevCountMismatch);
+        if (pos != rcnt && lane == 0) atomicExch(err, (int)kDevCountMismatch);
+        if (out + rcnt > cap && lane == 0) atomicExch(err, (int)kDevCapacity);
         int N = 1;
         while (N < pos) N <<= 1;
         const K kmax = sizeof(K) == 4 ? (K)0x7fffffff : (K)0x7fffffffffffffffLL;
         for (int s = pos + lane; s < N; s += 32) keys[s] = kmax;
         __syncwarp();
         warp_bitonic_sort<K, V>(keys, acc, N);
-        const int lim = min(pos, cnt);
+        const int lim = (int)max(0LL, min((long long)min(pos, rcnt), cap - out));
         for (int t = lane; t < lim; t += 32) {
             ciC[out + t] = (IT)keys[t];
             if constexpr (HV) vC[out + t] = acc[t];
@@ -400,19 +517,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // column >= the segment start in every B row).  Products go into a dense
 // accumulator acc[W] with presence flags, in ascending k; the chunk is then
 // emitted in column order.  Cursors live in a per-warp arena slot.
-constexpr int kSegGrid = 16;
-// Dense chunk configurations (columns per chunk, warps per block): one is
-// chosen per plan (spgemm_opts.reserved[0] = 1 or 2 forces one).
-constexpr int kDenseW0 = 1024, kDenseWarps0 = 8;
-constexpr int kDenseW1 = 2048, kDenseWarps1 = 4;
-constexpr int kMaxDenseClasses = kNumClasses - kClassDense0;
 
-struct DenseUnits {
-    int nclass;
-    int G[kMaxDenseClasses];
-    long long row_begin[kMaxDenseClasses];
-    long long unit_begin[kMaxDenseClasses + 1];
-};
 
 __host__ __device__ __forceinline__ long long seg_chunk(int g, int P) {
     return ((long long)g * P) / kSegGrid;
@@ -427,18 +532,24 @@ struct __align__(16) DenseCursor {
     int next_col;
 };
 
-// runlen[q] = number of entries from q to the end of q's column chunk
-// (col / W) inside its row of B: the length of the part of B(k,:) that a
-// chunk sweep consumes in one step.  One warp per row, windows of 32 from the
-// row end backwards.
+// runlen[run_base + q] = number of entries from q to the end of q's column
+// chunk (col / W) inside its row of B: the length of the part of B(k,:) that
+// a chunk sweep consumes in one step.  One warp per B row of every product,
+// windows of 32 from the row end backwards.
 template <class IT>
-__global__ void runlen_kernel(long long l, const int64_t* __restrict__ rpB,
-                              const IT* __restrict__ ciB, int W, int32_t* __restrict__ runlen) {
+__global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
+                              const long long* __restrict__ bb, int nprod, int W,
+                              int32_t* __restrict__ runlen) {
     const int lane = lane_id();
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < l; k += nwarps) {
-        const long long s0 = rpB[k], s1 = rpB[k + 1];
+    for (long long kb = warp; kb < LB; kb += nwarps) {
+        const int pr = nprod > 1 ? find_prod(bb, nprod, kb) : 0;
+        const ProdDesc& d = D[pr];
+        const long long k = kb - d.brow_base;
+        const IT* ciB = (const IT*)d.ciB;
+        int32_t* rl = runlen + d.run_base;
+        const long long s0 = d.rpB[k], s1 = d.rpB[k + 1];
         long long carry_end = s1;          // run end of the window after this one
         long long carry_chunk = -1;        // chunk of the first entry of that window
         for (long long hi = s1; hi > s0; hi -= 32) {
@@ -454,7 +565,7 @@ __global__ void runlen_kernel(long long l, const int64_t* __restrict__ rpB,
             long long end;
             if (ge) end = lo + (__ffs(ge) - 1) + 1;
             else end = carry_end;
-            if (in) runlen[q] = (int32_t)(end - q);
+            if (in) rl[q] = (int32_t)(end - q);
             // first entry of this window seeds the carry for the window before it
             carry_end = __shfl_sync(kFull, end, 0);
             carry_chunk = __shfl_sync(kFull, ch, 0);
@@ -462,41 +573,42 @@ __global__ void runlen_kernel(long long l, const int64_t* __restrict__ rpB,
     }
 }
 
-// segtab[k * (kSegGrid+1) + g] = first position p in B(k,:) with col >= seg_chunk(g)*W,
-// relative to rowptr[k].
+// segtab[seg_base + k * (kSegGrid+1) + g] = first position p in B(k,:) with
+// col >= seg_chunk(g, P) * W, relative to rowptr[k].
 template <class IT>
-__global__ void segtab_kernel(long long l, const int64_t* __restrict__ rpB,
-                              const IT* __restrict__ ciB, int W, int P,
+__global__ void segtab_kernel(long long LB, const ProdDesc* __restrict__ D,
+                              const long long* __restrict__ bb, int nprod, int W,
                               int32_t* __restrict__ segtab) {
-    const long long total = l * (kSegGrid + 1);
+    const long long total = LB * (kSegGrid + 1);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long k = t / (kSegGrid + 1);
-        const int g = (int)(t - k * (kSegGrid + 1));
-        const long long key = seg_chunk(g, P) * W;
-        long long lo = rpB[k], hi = rpB[k + 1];
+        const long long kb = t / (kSegGrid + 1);
+        const int g = (int)(t - kb * (kSegGrid + 1));
+        const int pr = nprod > 1 ? find_prod(bb, nprod, kb) : 0;
+        const ProdDesc& d = D[pr];
+        const long long k = kb - d.brow_base;
+        const IT* ciB = (const IT*)d.ciB;
+        const long long key = seg_chunk(g, d.P) * W;
+        long long lo = d.rpB[k], hi = d.rpB[k + 1];
         const long long base = lo;
         while (lo < hi) {
             long long mid = (lo + hi) >> 1;
             if ((long long)ciB[mid] < key) lo = mid + 1;
             else hi = mid;
         }
-        segtab[t] = (int32_t)(lo - base);
+        segtab[d.seg_base + k * (kSegGrid + 1) + g] = (int32_t)(lo - base);
     }
 }
 
 template <class IT, class V, int W, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-    numeric_dense_kernel(const int32_t* __restrict__ rows, DenseUnits U,
-                         const int64_t* __restrict__ rpA, const int64_t* __restrict__ reA,
-                         const IT* __restrict__ ciA, const V* __restrict__ vA,
-                         const int64_t* __restrict__ rpB, const IT* __restrict__ ciB,
-                         const V* __restrict__ vB, long long n, int P,
+    numeric_dense_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
                          const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
                          const int32_t* __restrict__ runlen, DenseCursor* __restrict__ arena,
-                         long long arena_stride,
-                         const int64_t* __restrict__ rpC, IT* __restrict__ ciC,
-                         V* __restrict__ vC, unsigned long long* work, int* err) {
+                         long long arena_stride, const int64_t* __restrict__ rpC, long long cap,
+                         IT* __restrict__ ciC, V* __restrict__ vC, unsigned long long* work,
+                         int* err) {
     constexpr bool HV = VOps<V>::has_val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
@@ -510,40 +622,62 @@ __global__ void __launch_bounds__(WARPS * 32)
         if constexpr (HV) acc[s] = VOps<V>::init();
     for (int s = lane; s < W / 32; s += 32) bm[s] = 0u;
     __syncwarp();
-    const long long total_units = U.unit_begin[U.nclass];
+    const unsigned long long* ub = cnt->unit_begin;
+    const long long total_units = (long long)ub[kMaxDenseClasses];
+    const int32_t* drow = rows + cnt->class_off[kClassDense0];
     while (true) {
         long long u = 0;
         if (lane == 0) u = (long long)atomicAdd(work, 1ull);
         u = __shfl_sync(kFull, u, 0);
         if (u >= total_units) break;
         int b = 0;
-        while (b + 1 < U.nclass && U.unit_begin[b + 1] <= u) ++b;
-        const int G = U.G[b];
-        const long long local = u - U.unit_begin[b];
-        const long long r = U.row_begin[b] + local / G;
+        while (b + 1 < kMaxDenseClasses && (long long)ub[b + 1] <= u) ++b;
+        const int G = dense_class_segments(b);
+        const long long local = u - (long long)ub[b];
+        const long long rr = (long long)(cnt->class_off[kClassDense0 + b] -
+                                         cnt->class_off[kClassDense0]) + local / G;
         const int seg = (int)(local % G);
+        const long long r = drow[rr];
+        const RowCtx<IT, V> cx = row_ctx<IT, V>(D, rb, nprod, r);
+        const int P = cx.P;
+        const long long n = cx.n;
         const int g0 = seg * (kSegGrid / G);
         const int cs = (int)seg_chunk(g0, P);
         const int ce = (int)seg_chunk(g0 + kSegGrid / G, P);
         if (cs >= ce) continue;
-        const long long i = rows[r];
-        const long long a0 = rpA[i], a1 = row_end(rpA, reA, i);
+        const long long a0 = cx.a0, a1 = cx.a1;
+        if (a1 - a0 > arena_stride) {
+            if (lane == 0) atomicExch(err, (int)kDevArena);
+            continue;
+        }
+        const IT* ciA = cx.ciA;
+        const V* vA = cx.vA;
+        const int64_t* rpB = cx.rpB;
+        const IT* ciB = cx.ciB;
+        const V* vB = cx.vB;
+        const int32_t* ccnt = chunkcnt + cx.chunk_base + cx.i * P;
+        const int32_t* stab = segtab + cx.seg_base;
+        const int32_t* rlen = runlen + cx.run_base;
         // output offset: row start plus the entries of the chunks before cs
         long long before = 0;
-        for (int c = lane; c < cs; c += 32) before += chunkcnt[r * P + c];
+        for (int c = lane; c < cs; c += 32) before += ccnt[c];
         before = warp_sum(before);
-        long long out = rpC[i] + before;
+        long long out = rpC[r] + before;
         long long seg_total = 0;
-        for (int c = cs + lane; c < ce; c += 32) seg_total += chunkcnt[r * P + c];
+        for (int c = cs + lane; c < ce; c += 32) seg_total += ccnt[c];
         seg_total = warp_sum(seg_total);
         if (seg_total == 0) continue;
         const long long out_end = out + seg_total;
+        if (out_end > cap) {
+            if (lane == 0) atomicExch(err, (int)kDevCapacity);
+            continue;
+        }
         // cursors at the segment start
         for (long long p = a0 + lane; p < a1; p += 32) {
             long long k = (long long)ciA[p];
             long long s0 = rpB[k];
             long long s1 = rpB[k + 1];
-            long long c0p = g0 == 0 ? s0 : s0 + segtab[k * (kSegGrid + 1) + g0];
+            long long c0p = g0 == 0 ? s0 : s0 + stab[k * (kSegGrid + 1) + g0];
             DenseCursor nc;
             nc.pos = c0p;
             nc.left = (int)(s1 - c0p);
@@ -552,7 +686,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         __syncwarp();
         for (int c = cs; c < ce; ++c) {
-            if (chunkcnt[r * P + c] == 0) continue;
+            if (ccnt[c] == 0) continue;
             const long long c0 = (long long)c * W;
             const long long c1 = min(c0 + (long long)W, n);
             for (long long bb = a0; bb < a1; bb += 32) {
@@ -566,7 +700,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 int len = 0;
                 V a = VOps<V>::init();
                 if (here) {
-                    len = runlen[cs2.pos];
+                    len = rlen[cs2.pos];
                     a = load_val(vA, p);
                 }
                 const long long cur = cs2.pos;

@@ -1,4 +1,7 @@
 // Template host launchers; included by the per-index-type instantiation units.
+// Every class kernel reads its row range from the device counters, so a
+// launch sequence needs no host readback (host-synced plans only use their
+// copies of the counts to skip empty classes and to size grids).
 #pragma once
 
 #include "plan.h"
@@ -26,18 +29,27 @@ inline long long grid_for(long long work_items, int per_block, int sm_count, int
     return std::max<long long>(1, std::min(need, cap));
 }
 
-template <class IT, class V, int W, int WARPS>
-cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC, IT* colC, V* valC);
+// Grid of a class kernel: the class's rows when known, one resident wave when not.
+inline long long class_grid(const Plan& P, long long rows_known, int per_block, int occ) {
+    if (P.device_sized) return (long long)P.sm_count * occ;
+    return grid_for(rows_known, per_block, P.sm_count, occ);
+}
+
+// Shared memory per warp of the dense numeric kernel (accumulator + bitmap).
+template <class V, int W>
+constexpr size_t dense_warp_bytes() {
+    return (VOps<V>::has_val ? sizeof(V) * W : 0) + W / 8;
+}
 
 template <class IT>
 cudaError_t launch_analyze(Plan& P) {
-    if (P.m <= 0) return cudaSuccess;
+    if (P.R <= 0) return cudaSuccess;
     auto k = analyze_kernel<IT>;
     int occ = occupancy_blocks(k, 256, 0);
-    long long g = grid_for(P.m, 8, P.sm_count, occ);
+    long long g = grid_for(P.R, 8, P.sm_count, occ);
     count_launches(1);
-    k<<<(unsigned)g, 256, 0, P.stream>>>(P.m, P.n, P.max_dense_n, P.A.rowptr, P.A.rowend,
-                                           (const IT*)P.A.col, P.B.rowptr, P.flops, P.cnt);
+    k<<<(unsigned)g, 256, 0, P.stream>>>(P.R, P.d_descs, P.rb, P.nprod, P.max_dense_n,
+                                           P.dense_min, P.flops, P.cls, P.cnt);
     return cudaGetLastError();
 }
 
@@ -69,109 +81,90 @@ cudaError_t sym_hash_bin(Plan& P, int bin, int64_t* rowcnt) {
     using K = typename KeyT<IT>::type;
     const int c = kClassHash0 + bin;
     const long long nrows = (long long)P.class_count[c];
-    if (nrows == 0) return cudaSuccess;
+    if (!P.device_sized && nrows == 0) return cudaSuccess;
+    if (P.device_sized && bin > 0 && hash_bin_flops(bin - 1) >= P.dense_min) return cudaSuccess;
     auto k = symbolic_hash_kernel<IT, LOG2T, WARPS>;
     size_t smem = (size_t)WARPS * (1u << LOG2T) * sizeof(K);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);
-    long long g = grid_for(nrows, WARPS, P.sm_count, occ);
+    long long g = class_grid(P, nrows, WARPS, occ);
     count_launches(1);
-    k<<<(unsigned)g, WARPS * 32, smem, P.stream>>>(
-        P.rows + P.class_off[c], nrows, P.A.rowptr, P.A.rowend, (const IT*)P.A.col, P.B.rowptr,
-        (const IT*)P.B.col, rowcnt, &P.cnt->err);
+    k<<<(unsigned)g, WARPS * 32, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt, c,
+                                                   rowcnt, &P.cnt->err);
     return cudaGetLastError();
 }
 
 template <class IT>
 cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
     WsLayout L = workspace_layout(P);
-    cudaError_t e = launch_zero_rows(P.rows + P.class_off[kClassEmpty],
-                                     (long long)P.class_count[kClassEmpty], rowcnt, P.sm_count,
-                                     P.stream);
+    cudaError_t e = launch_zero_rows(P, rowcnt);
     if (e != cudaSuccess) return e;
     if ((e = sym_hash_bin<IT, 6, 8>(P, 0, rowcnt)) != cudaSuccess) return e;
     if ((e = sym_hash_bin<IT, 8, 8>(P, 1, rowcnt)) != cudaSuccess) return e;
     if ((e = sym_hash_bin<IT, 10, 8>(P, 2, rowcnt)) != cudaSuccess) return e;
     if ((e = sym_hash_bin<IT, 11, 8>(P, 3, rowcnt)) != cudaSuccess) return e;
-    if (P.ndense > 0 && P.l > 0) {
-        long long total = P.l * (kSegGrid + 1);
+    const bool dense = P.device_sized || P.ndense > 0;
+    if (dense && P.LB > 0) {
+        long long total = P.LB * (kSegGrid + 1);
         long long g = grid_for(total, 256, P.sm_count, 8);
         count_launches(1);
-        segtab_kernel<IT><<<(unsigned)g, 256, 0, P.stream>>>(P.l, P.B.rowptr, (const IT*)P.B.col,
-                                                             P.W, P.P, (int32_t*)(ws + L.segtab));
+        segtab_kernel<IT><<<(unsigned)g, 256, 0, P.stream>>>(P.LB, P.d_descs, P.bb, P.nprod, P.W,
+                                                             (int32_t*)(ws + L.segtab));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        long long g2 = grid_for(P.l, 8, P.sm_count, 8);
+        long long g2 = grid_for(P.LB, 8, P.sm_count, 8);
         count_launches(1);
-        runlen_kernel<IT><<<(unsigned)g2, 256, 0, P.stream>>>(P.l, P.B.rowptr, (const IT*)P.B.col,
-                                                              P.W, (int32_t*)(ws + L.runlen));
+        runlen_kernel<IT><<<(unsigned)g2, 256, 0, P.stream>>>(P.LB, P.d_descs, P.bb, P.nprod, P.W,
+                                                              (int32_t*)(ws + L.runlen));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (P.ndense > 0) {
+    if (dense) {
         auto k = symbolic_dense_kernel<IT>;
         const int threads = 512;
-        size_t smem = (size_t)((P.n + 31) / 32) * 4;
+        const int max_words = (int)((P.max_n + 31) / 32);
+        size_t smem = (size_t)max_words * 4;
         if ((e = allow_smem(k, smem)) != cudaSuccess) return e;
         int occ = occupancy_blocks(k, threads, smem);
-        long long g = grid_for(P.ndense, 1, P.sm_count, occ);
+        long long g = class_grid(P, P.ndense, 1, occ);
         unsigned long long* work = &P.cnt->work_counter[0];
         if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), P.stream)) != cudaSuccess)
             return e;
         count_launches(1);
-        k<<<(unsigned)g, threads, smem, P.stream>>>(
-            P.rows + P.class_off[kClassDense0], P.ndense, P.A.rowptr, P.A.rowend,
-            (const IT*)P.A.col, P.B.rowptr, (const IT*)P.B.col, P.n, P.W / 32, P.P,
-            (int32_t*)(ws + L.chunkcnt), rowcnt, work);
+        k<<<(unsigned)g, threads, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt,
+                                                    max_words, P.W / 32,
+                                                    (int32_t*)(ws + L.chunkcnt), rowcnt, work);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 template <class IT, class V, int LOG2T, int WARPS>
-cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, IT* colC, V* valC) {
+cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT* colC,
+                         V* valC) {
     using K = typename KeyT<IT>::type;
     const int c = kClassHash0 + bin;
     const long long nrows = (long long)P.class_count[c];
-    if (nrows == 0) return cudaSuccess;
+    if (!P.device_sized && nrows == 0) return cudaSuccess;
+    if (P.device_sized && bin > 0 && hash_bin_flops(bin - 1) >= P.dense_min) return cudaSuccess;
     auto k = numeric_hash_kernel<IT, V, LOG2T, WARPS>;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
     size_t smem = (size_t)WARPS * (1u << LOG2T) * (sizeof(K) + vb);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);
-    long long g = grid_for(nrows, WARPS, P.sm_count, occ);
+    long long g = class_grid(P, nrows, WARPS, occ);
     count_launches(1);
-    k<<<(unsigned)g, WARPS * 32, smem, P.stream>>>(
-        P.rows + P.class_off[c], nrows, P.A.rowptr, P.A.rowend, (const IT*)P.A.col,
-        (const V*)P.A.val, P.B.rowptr, (const IT*)P.B.col, (const V*)P.B.val, rpC, colC, valC,
-        &P.cnt->err);
+    k<<<(unsigned)g, WARPS * 32, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt, c,
+                                                   rpC, cap, colC, valC, &P.cnt->err);
     return cudaGetLastError();
 }
 
-template <class IT, class V>
-cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, void* colC_,
-                           void* valC_) {
-    IT* colC = (IT*)colC_;
-    V* valC = (V*)valC_;
-    cudaError_t e;
-    if ((e = num_hash_bin<IT, V, 6, 8>(P, 0, rpC, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 8, 8>(P, 1, rpC, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 10, 8>(P, 2, rpC, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 11, 4>(P, 3, rpC, colC, valC)) != cudaSuccess) return e;
-    if (P.ndense > 0) {
-        e = P.W == kDenseW0 ? launch_numeric_dense<IT, V, kDenseW0, kDenseWarps0>(P, ws, rpC, colC, valC)
-                            : launch_numeric_dense<IT, V, kDenseW1, kDenseWarps1>(P, ws, rpC, colC, valC);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 template <class IT, class V, int W, int WARPS>
-cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC, IT* colC, V* valC) {
+cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
+                                 IT* colC, V* valC) {
     WsLayout L = workspace_layout(P);
     auto k = numeric_dense_kernel<IT, V, W, WARPS>;
-    constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t smem = (size_t)WARPS * (W * vb + W / 8);
+    size_t smem = (size_t)WARPS * dense_warp_bytes<V, W>();
     cudaError_t e;
     if ((e = allow_smem(k, smem)) != cudaSuccess) return e;
     unsigned long long* work = &P.cnt->work_counter[1];
@@ -179,25 +172,40 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
         return e;
     count_launches(1);
     k<<<(unsigned)P.dense_grid, WARPS * 32, smem, P.stream>>>(
-        P.rows + P.class_off[kClassDense0], P.units, P.A.rowptr, P.A.rowend,
-        (const IT*)P.A.col, (const V*)P.A.val, P.B.rowptr, (const IT*)P.B.col,
-        (const V*)P.B.val, P.n, P.P, (const int32_t*)(ws + L.chunkcnt),
+        P.d_descs, P.rb, P.nprod, P.rows, P.cnt, (const int32_t*)(ws + L.chunkcnt),
         (const int32_t*)(ws + L.segtab), (const int32_t*)(ws + L.runlen),
-        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, colC, valC, work, &P.cnt->err);
+        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, work, &P.cnt->err);
     return cudaGetLastError();
+}
+
+template <class IT, class V>
+cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
+                           void* colC_, void* valC_) {
+    IT* colC = (IT*)colC_;
+    V* valC = (V*)valC_;
+    cudaError_t e;
+    if ((e = num_hash_bin<IT, V, 6, 8>(P, 0, rpC, cap, colC, valC)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 8, 8>(P, 1, rpC, cap, colC, valC)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 10, 8>(P, 2, rpC, cap, colC, valC)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 11, 4>(P, 3, rpC, cap, colC, valC)) != cudaSuccess) return e;
+    if (P.device_sized || P.ndense > 0) {
+        e = P.W == kDenseW0
+                ? launch_numeric_dense<IT, V, kDenseW0, kDenseWarps0>(P, ws, rpC, cap, colC, valC)
+                : launch_numeric_dense<IT, V, kDenseW1, kDenseWarps1>(P, ws, rpC, cap, colC, valC);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <class IT, class V, int W, int WARPS>
 cudaError_t prepare_numeric_dense(Plan& P) {
     auto k = numeric_dense_kernel<IT, V, W, WARPS>;
-    constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t smem = (size_t)WARPS * (W * vb + W / 8);
+    size_t smem = (size_t)WARPS * dense_warp_bytes<V, W>();
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);
-    long long units = P.units.unit_begin[P.units.nclass];
     P.dense_warps_per_block = WARPS;
-    P.dense_grid = grid_for(std::max<long long>(units, 1), WARPS, P.sm_count, occ);
+    P.dense_grid = (long long)P.sm_count * occ;
     return cudaSuccess;
 }
 
@@ -220,12 +228,12 @@ cudaError_t prepare_numeric(Plan& P) {
     template cudaError_t prepare_numeric<IT, int64_t>(Plan&);                                  \
     template cudaError_t prepare_numeric<IT, NoVal>(Plan&);                                    \
     template cudaError_t launch_numeric<IT, double>(Plan&, unsigned char*, const int64_t*,     \
-                                                    void*, void*);                             \
+                                                    long long, void*, void*);                  \
     template cudaError_t launch_numeric<IT, float>(Plan&, unsigned char*, const int64_t*,      \
-                                                   void*, void*);                              \
+                                                   long long, void*, void*);                   \
     template cudaError_t launch_numeric<IT, int64_t>(Plan&, unsigned char*, const int64_t*,    \
-                                                     void*, void*);                            \
+                                                     long long, void*, void*);                 \
     template cudaError_t launch_numeric<IT, NoVal>(Plan&, unsigned char*, const int64_t*,      \
-                                                   void*, void*);
+                                                   long long, void*, void*);
 
 }  // namespace sg

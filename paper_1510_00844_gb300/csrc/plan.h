@@ -4,37 +4,49 @@
 #include <algorithm>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "../../include/spgemm.h"
 #include "kernels.cuh"
 
+// A plan covers a batch of products C_p = A_p . B_p (a single product is a
+// batch of one).  Rows of all products are numbered globally; the outputs
+// are the concatenation of the products' rows.
 struct spgemm_plan_s {
-    spgemm_csr A{}, B{};
     spgemm_opts opts{};
     cudaStream_t stream = nullptr;
     int it = 0;              // index type
     int vt = 0;              // value type used by the kernels (BOOL when pattern only)
-    long long m = 0, l = 0, n = 0;
+    int nprod = 0;
+    std::vector<sg::ProdDesc> descs;   // host copy
+    long long R = 0;         // total rows of the batch
+    long long LB = 0;        // total B rows of the batch
+    long long max_n = 0;     // largest n of the batch
     long long max_dense_n = 0;
+    int dense_min = 1024;    // rows with more products than this are dense
+    bool device_sized = false;  // no host readback: sizes are upper bounds
     // plan workspace
     unsigned char* pws = nullptr;
     size_t pws_bytes = 0;
     sg::DevCounters* cnt = nullptr;
+    sg::ProdDesc* d_descs = nullptr;
+    long long* rb = nullptr;       // row base prefix [nprod+1]
+    long long* bb = nullptr;       // B-row base prefix [nprod+1]
     int64_t* flops = nullptr;
+    unsigned char* cls = nullptr;
     int32_t* rows = nullptr;
-    // host copies of the row analysis
+    // host copies of the row analysis (host-synced plans)
     unsigned long long class_count[sg::kNumClasses] = {};
     long long class_off[sg::kNumClasses + 1] = {};
     long long total_flops = 0, max_flops = 0;
     long long ndense = 0;
-    int W = 2048;            // dense chunk width (columns)
-    int P = 1;               // chunks per dense row
-    long long max_dense_len = 0;  // longest A row among dense rows
+    int W = 1024;            // dense chunk width (columns)
+    long long max_dense_len = 0;  // cursor arena slot (entries)
     long long dense_grid = 0;     // blocks of the dense numeric kernel
-    int dense_warps_per_block = 4;
-    sg::DenseUnits units{};
+    int dense_warps_per_block = 8;
+    long long chunk_total = 0, seg_total = 0, run_total = 0;
     long long nnz_c = -1;
     int sm_count = 1;
     int smem_optin = 0;
@@ -52,14 +64,14 @@ struct WsLayout {
     size_t chunkcnt = 0, segtab = 0, runlen = 0, arena = 0, scan = 0, total = 0;
     long long arena_stride = 0;
 };
-void build_dense_units(Plan& P);
 WsLayout workspace_layout(const Plan& P);
+size_t plan_workspace_bytes(int nprod, long long R);
 
 size_t scan_temp_bytes(long long N);
 cudaError_t launch_exclusive_scan(int64_t* x, long long N, int64_t* temp, cudaStream_t s);
 cudaError_t launch_binning(Plan& P);
-cudaError_t launch_zero_rows(const int32_t* rows, long long nrows, int64_t* rowcnt, int sm_count,
-                             cudaStream_t s);
+cudaError_t launch_zero_rows(const Plan& P, int64_t* rowcnt);
+cudaError_t launch_product_rowptr(const Plan& P, const int64_t* g, int64_t* out);
 
 // Template launchers (instantiated per index type / value type).
 template <class IT>
@@ -71,7 +83,8 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt);
 template <class IT, class V>
 cudaError_t prepare_numeric(Plan& P);
 template <class IT, class V>
-cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, void* colC, void* valC);
+cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
+                           void* colC, void* valC);
 cudaError_t launch_merge(int c, const spgemm_csr* parts, int vt, long long m, long long n,
                          int sm_count, cudaStream_t s, bool numeric, int64_t* rowcnt,
                          const int64_t* rpC, void* colC, void* valC, int* err);

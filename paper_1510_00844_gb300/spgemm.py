@@ -43,7 +43,8 @@ class _Csr(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("semiring", ctypes.c_int32), ("checked", ctypes.c_int32),
-                ("dense_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("dense_chunk", ctypes.c_int32), ("dense_min_flops", ctypes.c_int32),
+                ("max_row_nnz", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Info(ctypes.Structure):
@@ -65,6 +66,13 @@ def _load():
         "spgemm_last_error": (ctypes.c_char_p, []),
         "spgemm_plan_workspace_size": (S, [I64_]),
         "spgemm_plan": (st, [P, P, P, P, P, S, P]),
+        "spgemm_batch_plan_workspace_size": (S, [I32_, P]),
+        "spgemm_batch_plan": (st, [I32_, P, P, P, P, P, S, P]),
+        "spgemm_plan_device": (st, [I32_, P, P, P, P, P, S, P]),
+        "spgemm_execute": (st, [P, P, S, P, I64_, P, P]),
+        "spgemm_batch_rowptrs": (st, [P, P, P]),
+        "spgemm_transpose_workspace_size": (S, [P]),
+        "spgemm_transpose": (st, [P, P, P, S, P, P, P]),
         "spgemm_plan_info": (st, [P, P]),
         "spgemm_workspace_size": (st, [P, P]),
         "spgemm_symbolic": (st, [P, P, S, P, P]),
@@ -215,10 +223,102 @@ def plan(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool =
     return Plan(A, B, semiring, checked, stream, dense_chunk)
 
 
+class BatchPlan(Plan):
+    """spgemm_batch_plan (device_sized=False) or spgemm_plan_device
+    (device_sized=True) over products C_p = As[p] . Bs[p]."""
+
+    def __init__(self, As: Sequence[DeviceCSR], Bs: Sequence[DeviceCSR], semiring: int = PLUS_TIMES,
+                 checked: bool = False, stream=None, dense_chunk: int = 0,
+                 dense_min_flops: int = 0, device_sized: bool = False, max_row_nnz: int = 0):
+        self.As, self.Bs = list(As), list(Bs)
+        self.A, self.B = self.As[0], self.Bs[0]
+        self.device = self.A.rowptr.device
+        self.count = len(self.As)
+        self._cAs = (_Csr * self.count)(*[_csr(M) for M in self.As])
+        self._cBs = (_Csr * self.count)(*[_csr(M) for M in self.Bs])
+        self._opts = _Opts(semiring, 1 if checked else 0, dense_chunk, dense_min_flops, max_row_nnz)
+        self.pattern_only = semiring == OR_AND or self.A.val is None
+        self.stream = stream
+        self.device_sized = device_sized
+        self.rows = [M.nrows for M in self.As]
+        self.row_base = np.concatenate([[0], np.cumsum(self.rows)]).astype(np.int64)
+        self.R = int(self.row_base[-1])
+        nbytes = _lib.spgemm_batch_plan_workspace_size(self.count, self._cAs)
+        self._plan_ws = _workspace(nbytes, self.device)
+        h = ctypes.c_void_p()
+        fn = _lib.spgemm_plan_device if device_sized else _lib.spgemm_batch_plan
+        _check(fn(self.count, self._cAs, self._cBs, ctypes.byref(self._opts), _stream(stream),
+                  ctypes.c_void_p(self._plan_ws.data_ptr()), self._plan_ws.numel(),
+                  ctypes.byref(h)))
+        self._h = h
+        nb = ctypes.c_size_t()
+        _check(_lib.spgemm_workspace_size(self._h, ctypes.byref(nb)))
+        self.ws = _workspace(nb.value, self.device)
+
+
+def batch_plan(As, Bs, semiring: int = PLUS_TIMES, checked: bool = False, stream=None,
+               dense_chunk: int = 0, dense_min_flops: int = 0) -> BatchPlan:
+    return BatchPlan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops)
+
+
+def device_plan(As, Bs, semiring: int = PLUS_TIMES, stream=None, dense_chunk: int = 0,
+                dense_min_flops: int = 0, max_row_nnz: int = 0) -> BatchPlan:
+    return BatchPlan(As, Bs, semiring, False, stream, dense_chunk, dense_min_flops,
+                     device_sized=True, max_row_nnz=max_row_nnz)
+
+
+def execute(p: BatchPlan, rowptrC: torch.Tensor, capacity: int, colC: torch.Tensor,
+            valC: Optional[torch.Tensor]) -> None:
+    """spgemm_execute: the whole batch enqueued with no host readback."""
+    _check(_lib.spgemm_execute(p._h, ctypes.c_void_p(p.ws.data_ptr()), p.ws.numel(),
+                               ctypes.c_void_p(rowptrC.data_ptr()), int(capacity),
+                               ctypes.c_void_p(colC.data_ptr()) if colC.numel() else None,
+                               None if valC is None or valC.numel() == 0
+                               else ctypes.c_void_p(valC.data_ptr())))
+
+
+def batch_rowptrs(p: BatchPlan, rowptrC: torch.Tensor) -> torch.Tensor:
+    """Per-product row pointers (each m_p + 1 entries, one after the other)."""
+    out = torch.empty(p.R + p.count, dtype=torch.int64, device=p.device)
+    _check(_lib.spgemm_batch_rowptrs(p._h, ctypes.c_void_p(rowptrC.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr())))
+    return out
+
+
+def split_batch(p: BatchPlan, rowptrC: torch.Tensor, colC: torch.Tensor,
+                valC: Optional[torch.Tensor]) -> List[DeviceCSR]:
+    """Views of the products of a batch result (no copy of columns/values)."""
+    rps = batch_rowptrs(p, rowptrC)
+    starts = rowptrC[torch.as_tensor(p.row_base, device=p.device)].cpu().numpy()
+    out = []
+    for q in range(p.count):
+        m = p.rows[q]
+        rp = rps[p.row_base[q] + q: p.row_base[q] + q + m + 1]
+        a, b = int(starts[q]), int(starts[q + 1])
+        out.append(DeviceCSR(m, p.Bs[q].ncols, rp, colC[a:b],
+                             None if valC is None else valC[a:b]))
+    return out
+
+
+def batch_spgemm(As, Bs, semiring: int = PLUS_TIMES, checked: bool = False, stream=None,
+                 verify: bool = False, dense_chunk: int = 0,
+                 dense_min_flops: int = 0) -> List[DeviceCSR]:
+    """All products C_p = As[p] . Bs[p] with one plan (one launch per phase)."""
+    p = batch_plan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops)
+    rowptrC, nnz = symbolic(p)
+    colC, valC = alloc_output(p, nnz)
+    numeric(p, rowptrC, colC, valC)
+    if verify:
+        check(p)
+    res = split_batch(p, rowptrC, colC, valC)
+    p.close()
+    return res
+
+
 def symbolic(p: Plan, rowptrC: Optional[torch.Tensor] = None):
     """Row pointers of C and nnz(C) (waits for the stream)."""
     if rowptrC is None:
-        rowptrC = torch.empty(p.A.nrows + 1, dtype=torch.int64, device=p.device)
+        rowptrC = torch.empty(getattr(p, "R", p.A.nrows) + 1, dtype=torch.int64, device=p.device)
     nnz = ctypes.c_int64()
     _check(_lib.spgemm_symbolic(p._h, ctypes.c_void_p(p.ws.data_ptr()), p.ws.numel(),
                                 ctypes.c_void_p(rowptrC.data_ptr()), ctypes.byref(nnz)))
@@ -255,6 +355,20 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool
         check(p)
     p.close()
     return DeviceCSR(A.nrows, B.ncols, rowptrC, colC, valC)
+
+
+def transpose(A: DeviceCSR, stream=None) -> DeviceCSR:
+    """A^T with ascending columns (spgemm_transpose)."""
+    cA = _csr(A)
+    ws = _workspace(_lib.spgemm_transpose_workspace_size(ctypes.byref(cA)), A.rowptr.device)
+    rp = torch.empty(A.ncols + 1, dtype=torch.int64, device=A.rowptr.device)
+    col = torch.empty(A.nnz, dtype=A.col.dtype, device=A.rowptr.device)
+    val = None if A.val is None else torch.empty(A.nnz, dtype=A.val.dtype, device=A.rowptr.device)
+    _check(_lib.spgemm_transpose(ctypes.byref(cA), _stream(stream), ctypes.c_void_p(ws.data_ptr()),
+                                 ws.numel(), ctypes.c_void_p(rp.data_ptr()),
+                                 ctypes.c_void_p(col.data_ptr()) if A.nnz else None,
+                                 None if val is None or A.nnz == 0 else ctypes.c_void_p(val.data_ptr())))
+    return DeviceCSR(A.ncols, A.nrows, rp, col, val)
 
 
 def kslice_bounds(A: DeviceCSR, c: int, stream=None) -> torch.Tensor:
