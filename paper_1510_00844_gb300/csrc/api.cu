@@ -225,10 +225,6 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->chunk_total = chunk;
     P->seg_total = seg;
     P->run_total = run;
-    if (device_sized && P->max_n > P->max_dense_n)
-        return bail(fail(SPGEMM_ERR_NOT_SUPPORTED,
-                         "device-sized plans need n <= %lld columns in every product (n = %lld)",
-                         P->max_dense_n, P->max_n));
     // plan workspace layout
     P->pws = (unsigned char*)plan_ws;
     P->pws_bytes = plan_ws_bytes;
@@ -514,6 +510,10 @@ spgemm_status spgemm_check(spgemm_plan_t P) {
     if (herr == sg::kDevCapacity) return fail(SPGEMM_ERR_OUT_OF_MEMORY, "C did not fit the output capacity");
     if (herr == sg::kDevArena)
         return fail(SPGEMM_ERR_NOT_SUPPORTED, "a dense row of A is longer than max_row_nnz");
+    if (herr == sg::kDevTooWide)
+        return fail(SPGEMM_ERR_NOT_SUPPORTED,
+                    "a row with more than dense_min_flops products in a product with more "
+                    "columns than the shared-memory bitmap holds");
     if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed (code %d)", herr);
     return SPGEMM_OK;
 }

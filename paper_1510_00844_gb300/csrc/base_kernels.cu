@@ -23,13 +23,28 @@ __global__ void class_offsets_kernel(DevCounters* cnt) {
 }
 
 // Scatter global row ids into their class segment (order inside a class is
-// free; rows are independent).
+// free; rows are independent).  Each block counts its rows per class in
+// shared memory, reserves one range per class with a single global atomic,
+// then places its rows.
 __global__ void bin_rows_kernel(long long R, const unsigned char* __restrict__ cls,
                                 int32_t* __restrict__ rows, DevCounters* cnt) {
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R;
-         r += (long long)gridDim.x * blockDim.x) {
-        unsigned long long pos = atomicAdd(&cnt->class_cursor[cls[r]], 1ull);
-        rows[pos] = (int32_t)r;
+    __shared__ unsigned long long loc[kNumClasses];
+    __shared__ unsigned long long base[kNumClasses];
+    const long long per_block = (R + gridDim.x - 1) / gridDim.x;
+    const long long r0 = (long long)blockIdx.x * per_block;
+    const long long r1 = min(R, r0 + per_block);
+    for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) loc[t] = 0;
+    __syncthreads();
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(&loc[cls[r]], 1ull);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) {
+        base[t] = loc[t] ? atomicAdd(&cnt->class_cursor[t], loc[t]) : 0;
+        loc[t] = 0;
+    }
+    __syncthreads();
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int c = cls[r];
+        rows[base[c] + atomicAdd(&loc[c], 1ull)] = (int32_t)r;
     }
 }
 
@@ -140,7 +155,7 @@ cudaError_t launch_binning(Plan& P) {
     count_launches(1);
     class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt);
     if (R > 0) {
-        int blocks = (int)std::min<long long>((R + 255) / 256, (long long)P.sm_count * 8);
+        int blocks = (int)std::max<long long>(1, std::min<long long>((R + 1023) / 1024, (long long)P.sm_count * 4));
         count_launches(1);
         bin_rows_kernel<<<blocks, 256, 0, P.stream>>>(R, P.cls, P.rows, P.cnt);
     }

@@ -302,12 +302,12 @@ __global__ void __launch_bounds__(WARPS * 32)
 // per-chunk counts chunkcnt[chunk_base + i*P + c] (chunk c covers columns
 // [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
 template <class IT>
-__global__ void symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+__global__ void __launch_bounds__(512, 3) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
                                       const long long* __restrict__ rb, int nprod,
                                       const int32_t* __restrict__ rows, const DevCounters* cnt,
                                       int max_words, int chunk_words,
                                       int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
-                                      unsigned long long* work) {
+                                      unsigned long long* work, int* err) {
     extern __shared__ unsigned bm[];
     __shared__ long long row_total;
     __shared__ long long cur_row;
@@ -334,6 +334,11 @@ __global__ void symbolic_dense_kernel(const ProdDesc* __restrict__ D,
         const IT* ciB = cx.ciB;
         const int NW = (int)((cx.n + 31) >> 5);
         const int P = cx.P;
+        if (NW > max_words) {  // n beyond the shared-memory bitmap: reported, row skipped
+            if (threadIdx.x == 0) atomicExch(err, (int)kDevTooWide);
+            __syncthreads();
+            continue;
+        }
         for (long long b = a0 + (long long)w * 32; b < a1; b += (long long)nwarps * 32) {
             const int nb = (int)min(32LL, a1 - b);
             long long lo = 0;
@@ -404,6 +409,65 @@ __device__ __forceinline__ void warp_bitonic_sort(K* keys, V* vals, int N) {
     }
 }
 
+// Stable LSD radix sort of N (key, value) pairs by one warp, 8-bit digits
+// over the low `bits` bits of the keys (keys are >= 0).  Ping-pongs between
+// (k0, v0) and (k1, v1); returns true if the sorted pairs end in (k1, v1).
+// Each pass: digit histogram, exclusive scan, then a scatter in rounds of 32
+// keys in input order where lanes with equal digits take consecutive slots
+// in lane order, so equal digits keep their input order.
+template <class K, class V>
+__device__ __forceinline__ bool warp_radix_sort(K* k0, V* v0, K* k1, V* v1, int N, int bits,
+                                                int* cnt) {
+    constexpr bool HV = VOps<V>::has_val;
+    const int lane = lane_id();
+    bool flip = false;
+    for (int shift = 0; shift < bits; shift += 8) {
+        K* kin = flip ? k1 : k0;
+        V* vin = flip ? v1 : v0;
+        K* kout = flip ? k0 : k1;
+        V* vout = flip ? v0 : v1;
+        for (int t = lane; t < 256; t += 32) cnt[t] = 0;
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) atomicAdd(&cnt[(int)((kin[i] >> shift) & 255)], 1);
+        __syncwarp();
+        int loc[8];
+        int sum = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            loc[t] = cnt[lane * 8 + t];
+            sum += loc[t];
+        }
+        int run = warp_incl_scan(sum) - sum;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            cnt[lane * 8 + t] = run;
+            run += loc[t];
+        }
+        __syncwarp();
+        for (int i0 = 0; i0 < N; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < N;
+            K kk = valid ? kin[i] : K(0);
+            V vv{};
+            if constexpr (HV)
+                if (valid) vv = vin[i];
+            const int d = valid ? (int)((kk >> shift) & 255) : 256 + lane;
+            const unsigned grp = __match_any_sync(kFull, d);
+            const int rank = __popc(grp & lanemask_lt());
+            const int base = valid ? cnt[d] : 0;
+            __syncwarp();
+            if (valid) {
+                kout[base + rank] = kk;
+                if constexpr (HV) vout[base + rank] = vv;
+                if ((grp >> lane) == 1u) cnt[d] = base + __popc(grp);  // highest lane of the group
+            }
+            __syncwarp();
+        }
+        flip = !flip;
+    }
+    return flip;
+}
+
 // One warp per row; table of 2^LOG2T (key, value) slots; products added in
 // ascending k (ordered rounds); table compacted, sorted, written.
 template <class IT, class V, int LOG2T, int WARPS>
@@ -418,11 +482,12 @@ __global__ void __launch_bounds__(WARPS * 32)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
-    // layout per warp: T values (if any) then T keys
+    // layout per warp: T values (if any), T keys, 256 radix counters
     constexpr size_t vbytes = HV ? sizeof(V) * T : 0;
-    unsigned char* base = smem_raw + (size_t)w * (vbytes + sizeof(K) * T);
+    unsigned char* base = smem_raw + (size_t)w * (vbytes + sizeof(K) * T + 256 * sizeof(int));
     V* acc = reinterpret_cast<V*>(base);
     K* keys = reinterpret_cast<K*>(base + vbytes);
+    int* rcnt_smem = reinterpret_cast<int*>(base + vbytes + sizeof(K) * T);
     for (int s = lane; s < T; s += 32) {
         keys[s] = K(-1);
         if constexpr (HV) acc[s] = VOps<V>::init();
@@ -487,16 +552,29 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         if (pos != rcnt && lane == 0) atomicExch(err, (int)kDevCountMismatch);
         if (out + rcnt > cap && lane == 0) atomicExch(err, (int)kDevCapacity);
-        int N = 1;
-        while (N < pos) N <<= 1;
-        const K kmax = sizeof(K) == 4 ? (K)0x7fffffff : (K)0x7fffffffffffffffLL;
-        for (int s = pos + lane; s < N; s += 32) keys[s] = kmax;
-        __syncwarp();
-        warp_bitonic_sort<K, V>(keys, acc, N);
+        const K* sk = keys;
+        const V* sv = acc;
+        if (pos <= 64) {
+            int N = 1;
+            while (N < pos) N <<= 1;
+            const K kmax = sizeof(K) == 4 ? (K)0x7fffffff : (K)0x7fffffffffffffffLL;
+            for (int s = pos + lane; s < N; s += 32) keys[s] = kmax;
+            __syncwarp();
+            warp_bitonic_sort<K, V>(keys, acc, N);
+        } else {
+            // pos <= T/2: the upper half of the table is the second buffer
+            const int bits = c.n > 1 ? 64 - __clzll((unsigned long long)(c.n - 1)) : 1;
+            const bool in_upper = warp_radix_sort<K, V>(keys, acc, keys + T / 2, acc + T / 2, pos,
+                                                        bits, rcnt_smem);
+            if (in_upper) {
+                sk = keys + T / 2;
+                sv = acc + T / 2;
+            }
+        }
         const int lim = (int)max(0LL, min((long long)min(pos, rcnt), cap - out));
         for (int t = lane; t < lim; t += 32) {
-            ciC[out + t] = (IT)keys[t];
-            if constexpr (HV) vC[out + t] = acc[t];
+            ciC[out + t] = (IT)sk[t];
+            if constexpr (HV) vC[out + t] = sv[t];
         }
         __syncwarp();
         for (int s = lane; s < T; s += 32) {
@@ -539,7 +617,8 @@ struct __align__(16) DenseCursor {
 template <class IT>
 __global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
                               const long long* __restrict__ bb, int nprod, int W,
-                              int32_t* __restrict__ runlen) {
+                              int32_t* __restrict__ runlen, const DevCounters* cnt) {
+    if (cnt->class_off[kNumClasses] == cnt->class_off[kClassDense0]) return;  // no dense rows
     const int lane = lane_id();
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -578,7 +657,8 @@ __global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
 template <class IT>
 __global__ void segtab_kernel(long long LB, const ProdDesc* __restrict__ D,
                               const long long* __restrict__ bb, int nprod, int W,
-                              int32_t* __restrict__ segtab) {
+                              int32_t* __restrict__ segtab, const DevCounters* cnt) {
+    if (cnt->class_off[kNumClasses] == cnt->class_off[kClassDense0]) return;  // no dense rows
     const long long total = LB * (kSegGrid + 1);
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -607,8 +687,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                          const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
                          const int32_t* __restrict__ runlen, DenseCursor* __restrict__ arena,
                          long long arena_stride, const int64_t* __restrict__ rpC, long long cap,
-                         IT* __restrict__ ciC, V* __restrict__ vC, unsigned long long* work,
-                         int* err) {
+                         IT* __restrict__ ciC, V* __restrict__ vC, long long max_dense_n,
+                         unsigned long long* work, int* err) {
     constexpr bool HV = VOps<V>::has_val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
@@ -641,6 +721,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         const RowCtx<IT, V> cx = row_ctx<IT, V>(D, rb, nprod, r);
         const int P = cx.P;
         const long long n = cx.n;
+        if (n > max_dense_n) continue;
         const int g0 = seg * (kSegGrid / G);
         const int cs = (int)seg_chunk(g0, P);
         const int ce = (int)seg_chunk(g0 + kSegGrid / G, P);

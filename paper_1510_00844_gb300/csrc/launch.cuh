@@ -110,18 +110,18 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
         long long g = grid_for(total, 256, P.sm_count, 8);
         count_launches(1);
         segtab_kernel<IT><<<(unsigned)g, 256, 0, P.stream>>>(P.LB, P.d_descs, P.bb, P.nprod, P.W,
-                                                             (int32_t*)(ws + L.segtab));
+                                                             (int32_t*)(ws + L.segtab), P.cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         long long g2 = grid_for(P.LB, 8, P.sm_count, 8);
         count_launches(1);
         runlen_kernel<IT><<<(unsigned)g2, 256, 0, P.stream>>>(P.LB, P.d_descs, P.bb, P.nprod, P.W,
-                                                              (int32_t*)(ws + L.runlen));
+                                                              (int32_t*)(ws + L.runlen), P.cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (dense) {
         auto k = symbolic_dense_kernel<IT>;
         const int threads = 512;
-        const int max_words = (int)((P.max_n + 31) / 32);
+        const int max_words = (int)((std::min(P.max_n, P.max_dense_n) + 31) / 32);
         size_t smem = (size_t)max_words * 4;
         if ((e = allow_smem(k, smem)) != cudaSuccess) return e;
         int occ = occupancy_blocks(k, threads, smem);
@@ -132,7 +132,8 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
         count_launches(1);
         k<<<(unsigned)g, threads, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt,
                                                     max_words, P.W / 32,
-                                                    (int32_t*)(ws + L.chunkcnt), rowcnt, work);
+                                                    (int32_t*)(ws + L.chunkcnt), rowcnt, work,
+                                                    &P.cnt->err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -148,7 +149,7 @@ cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT
     if (P.device_sized && bin > 0 && hash_bin_flops(bin - 1) >= P.dense_min) return cudaSuccess;
     auto k = numeric_hash_kernel<IT, V, LOG2T, WARPS>;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t smem = (size_t)WARPS * (1u << LOG2T) * (sizeof(K) + vb);
+    size_t smem = (size_t)WARPS * ((1u << LOG2T) * (sizeof(K) + vb) + 256 * sizeof(int));
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);
@@ -174,7 +175,8 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
     k<<<(unsigned)P.dense_grid, WARPS * 32, smem, P.stream>>>(
         P.d_descs, P.rb, P.nprod, P.rows, P.cnt, (const int32_t*)(ws + L.chunkcnt),
         (const int32_t*)(ws + L.segtab), (const int32_t*)(ws + L.runlen),
-        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, work, &P.cnt->err);
+        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, P.max_dense_n, work,
+        &P.cnt->err);
     return cudaGetLastError();
 }
 

@@ -46,10 +46,12 @@ __global__ void scatter_kernel(long long m, const int64_t* __restrict__ rp,
 }
 
 // Sorts rows of A^T with length in (lo, hi]; WARP_ROWS: one warp per row
-// (hi <= 1024), else one block per row (hi <= 8192).  Keys are unique.
+// (hi <= 1024), which also lists the longer rows; else one block per listed
+// row (hi <= 8192).  Keys are unique.
 template <class IT, class V, bool WARP_ROWS, int CAP>
 __global__ void sort_rows_kernel(long long n, const int64_t* __restrict__ rpT, int lo, int hi,
-                                 IT* __restrict__ ciT, V* __restrict__ vaT) {
+                                 IT* __restrict__ ciT, V* __restrict__ vaT,
+                                 long long* __restrict__ long_rows, unsigned* long_count) {
     constexpr bool HV = VOps<V>::has_val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
@@ -64,9 +66,15 @@ __global__ void sort_rows_kernel(long long n, const int64_t* __restrict__ rpT, i
     const long long step = WARP_ROWS ? (long long)gridDim.x * nwarps : gridDim.x;
     const int t0 = WARP_ROWS ? lane : threadIdx.x;
     const int tstep = WARP_ROWS ? 32 : blockDim.x;
-    for (long long j = first; j < n; j += step) {
+    const long long nitems = WARP_ROWS ? n : (long long)*long_count;
+    for (long long it = first; it < nitems; it += step) {
+        const long long j = WARP_ROWS ? it : long_rows[it];
         const long long a = rpT[j];
         const int L = (int)(rpT[j + 1] - a);
+        if (L > hi && WARP_ROWS && long_rows) {   // handed to the block pass
+            if (lane == 0) long_rows[atomicAdd(long_count, 1u)] = j;
+            continue;
+        }
         if (L <= lo || L > hi) continue;
         int N = 1;
         while (N < L) N <<= 1;
@@ -108,10 +116,13 @@ __global__ void sort_rows_kernel(long long n, const int64_t* __restrict__ rpT, i
 // Rows longer than 8192: each entry's position is the number of smaller keys
 // in its row (keys are unique); results go to a scratch copy, then back.
 template <class IT, class V>
-__global__ void rank_rows_kernel(long long n, const int64_t* __restrict__ rpT, int lo,
-                                 const IT* __restrict__ ciT, const V* __restrict__ vaT,
+__global__ void rank_rows_kernel(const long long* __restrict__ long_rows,
+                                 const unsigned* long_count, const int64_t* __restrict__ rpT,
+                                 int lo, const IT* __restrict__ ciT, const V* __restrict__ vaT,
                                  IT* __restrict__ ciS, V* __restrict__ vaS) {
-    for (long long j = blockIdx.x; j < n; j += gridDim.x) {
+    const long long nitems = (long long)*long_count;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const long long j = long_rows[it];
         const long long a = rpT[j];
         const long long L = rpT[j + 1] - a;
         if (L <= lo) continue;
@@ -126,10 +137,13 @@ __global__ void rank_rows_kernel(long long n, const int64_t* __restrict__ rpT, i
 }
 
 template <class IT, class V>
-__global__ void copy_back_kernel(long long n, const int64_t* __restrict__ rpT, int lo,
-                                 const IT* __restrict__ ciS, const V* __restrict__ vaS,
+__global__ void copy_back_kernel(const long long* __restrict__ long_rows,
+                                 const unsigned* long_count, const int64_t* __restrict__ rpT,
+                                 int lo, const IT* __restrict__ ciS, const V* __restrict__ vaS,
                                  IT* __restrict__ ciT, V* __restrict__ vaT) {
-    for (long long j = blockIdx.x; j < n; j += gridDim.x) {
+    const long long nitems = (long long)*long_count;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const long long j = long_rows[it];
         const long long a = rpT[j];
         const long long L = rpT[j + 1] - a;
         if (L <= lo) continue;
@@ -151,6 +165,13 @@ cudaError_t launch_transpose(const spgemm_csr& A, cudaStream_t s, unsigned char*
     V* vaT = (V*)vaT_;
     unsigned long long* cursor = (unsigned long long*)ws;
     int64_t* temp = (int64_t*)(ws + ((size_t)(n + 1) * 8 + 255) / 256 * 256);
+    const size_t isz = sizeof(IT), vsz = VOps<V>::has_val ? sizeof(V) : 0;
+    unsigned char* after_scratch = ws + ((size_t)(n + 1) * 8 + 255) / 256 * 256 +
+                                   (scan_temp_bytes(n + 1) + 255) / 256 * 256 +
+                                   ((size_t)nnz * isz + 255) / 256 * 256 +
+                                   ((size_t)nnz * vsz + 255) / 256 * 256;
+    unsigned* long_count = (unsigned*)after_scratch;
+    long long* long_rows = (long long*)(after_scratch + 256);
     cudaError_t e;
     if ((e = cudaMemsetAsync(rpT, 0, (size_t)(n + 1) * sizeof(int64_t), s)) != cudaSuccess) return e;
     auto blocks = [&](long long items, int per) {
@@ -171,6 +192,7 @@ cudaError_t launch_transpose(const spgemm_csr& A, cudaStream_t s, unsigned char*
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (n <= 0 || nnz <= 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(long_count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
     {
         auto k = sort_rows_kernel<IT, V, true, 1024>;
@@ -179,7 +201,7 @@ cudaError_t launch_transpose(const spgemm_csr& A, cudaStream_t s, unsigned char*
             (e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         count_launches(1);
-        k<<<blocks(n, 4), 128, smem, s>>>(n, rpT, 1, 1024, ciT, vaT);
+        k<<<blocks(n, 4), 128, smem, s>>>(n, rpT, 1, 1024, ciT, vaT, long_rows, long_count);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
@@ -188,8 +210,8 @@ cudaError_t launch_transpose(const spgemm_csr& A, cudaStream_t s, unsigned char*
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         count_launches(1);
-        k<<<(unsigned)std::min<long long>(n, (long long)sms * 2), 512, smem, s>>>(n, rpT, 1024, 8192,
-                                                                                ciT, vaT);
+        k<<<(unsigned)std::min<long long>(n, (long long)sms * 2), 512, smem, s>>>(
+            n, rpT, 1024, 8192, ciT, vaT, long_rows, long_count);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
@@ -198,8 +220,8 @@ cudaError_t launch_transpose(const spgemm_csr& A, cudaStream_t s, unsigned char*
         V* vaS = (V*)((unsigned char*)ciS + ((size_t)nnz * sizeof(IT) + 255) / 256 * 256);
         const unsigned g = (unsigned)std::min<long long>(n, (long long)sms * 4);
         count_launches(2);
-        rank_rows_kernel<IT, V><<<g, 256, 0, s>>>(n, rpT, 8192, ciT, vaT, ciS, vaS);
-        copy_back_kernel<IT, V><<<g, 256, 0, s>>>(n, rpT, 8192, ciS, vaS, ciT, vaT);
+        rank_rows_kernel<IT, V><<<g, 256, 0, s>>>(long_rows, long_count, rpT, 8192, ciT, vaT, ciS, vaS);
+        copy_back_kernel<IT, V><<<g, 256, 0, s>>>(long_rows, long_count, rpT, 8192, ciS, vaS, ciT, vaT);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -216,7 +238,8 @@ size_t spgemm_transpose_workspace_size(const spgemm_csr* A) {
     const size_t isz = A->index_type == SPGEMM_INDEX_I32 ? 4 : 8;
     const size_t vsz = A->value_type == SPGEMM_F32 ? 4 : A->value_type == SPGEMM_BOOL ? 0 : 8;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    return al((n + 1) * 8) + al(sg::scan_temp_bytes((long long)n + 1)) + al(nnz * isz) + al(nnz * vsz);
+    return al((n + 1) * 8) + al(sg::scan_temp_bytes((long long)n + 1)) + al(nnz * isz) +
+           al(nnz * vsz) + 256 + al((n + 1) * 8);
 }
 
 spgemm_status spgemm_transpose(const spgemm_csr* A, void* stream, void* ws, size_t ws_bytes,
