@@ -217,6 +217,7 @@ def run_ours(args):
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
     traffic = profiled_traffic()
 
+    paths = run_paths(args, A, dA, sg, torch) if (rank == 0 and world == 1 and not args.no_paths) else None
     e2e = (run_e2e(args, A, sg, torch, dev, dP if world == 1 else None)
            if rank == 0 and not args.no_e2e else None)
     cpu = run_cpu_baseline(A) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -237,6 +238,7 @@ def run_ours(args):
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": peak_src,
                          "algorithmic_bytes": num_bytes, "traffic": traffic},
+            "paths": paths,
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": e2e,
@@ -245,6 +247,77 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed(torch, fn, reps):
+    """Wall time of fn() with a device synchronize on both sides (best of reps)."""
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        del out
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def run_paths(args, A, dA, sg, torch):
+    """The other rows of the path, each against its plain counterpart:
+    k=4 split + merge on the same product, 512 uneven ER products batched vs
+    one by one, and the AMG Galerkin hierarchy in one CUDA graph vs the
+    host-synced chain."""
+    from paper_1510_00844_gb300 import amg, inputs
+    out = {}
+    reps = 2
+    flops = sg.plan(dA, dA).info()["flops"]
+    _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4), 1)
+    t = _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4), reps)
+    out["kslice4_merge_rmat18"] = {"ms": round(t * 1e3, 3),
+                                   "gflops": round(2 * flops / t / 1e9, 3),
+                                   "note": "4 k-slice partial products + multiway merge"}
+    pairs = inputs.batched_er(512)
+    As = [sg.to_device(a) for a, _ in pairs]
+    Bs = [sg.to_device(b) for _, b in pairs]
+    bflops = sg.batch_plan(As, Bs).info()["flops"]
+    _timed(torch, lambda: sg.batch_spgemm(As, Bs), 1)
+    tb = _timed(torch, lambda: sg.batch_spgemm(As, Bs), reps)
+    ts = _timed(torch, lambda: [sg.spgemm(a, b) for a, b in zip(As, Bs)], reps)
+    out["batched_er512_f32"] = {"batched_ms": round(tb * 1e3, 3), "sequential_ms": round(ts * 1e3, 3),
+                                "speedup": round(ts / tb, 3), "flops": int(bflops),
+                                "gflops_batched": round(2 * bflops / tb / 1e9, 3)}
+    del As, Bs, pairs
+    N = 128
+    A0 = inputs.laplacian_7pt(N)
+    Rs = [inputs.aggregation_2x2x2(N >> l) for l in range(3)]
+    dA0 = sg.to_device(A0)
+    dRs = [sg.to_device(R) for R in Rs]
+    s = torch.cuda.Stream()
+    chain = amg.GalerkinChain(dA0, dRs, s)
+    chain.capture()
+    tg = _timed(torch, chain.replay, 5)
+    chain.check()
+
+    def plain_chain():
+        A_ = dA0
+        for R in dRs:
+            A_ = sg.spgemm(sg.spgemm(sg.transpose(R), A_), R)
+        return A_
+    plain_chain()
+    tp = _timed(torch, plain_chain, 5)
+    gflops = 0
+    A_ = dA0
+    for R in dRs:
+        Rt = sg.transpose(R)
+        gflops += sg.plan(Rt, A_).info()["flops"]
+        T = sg.spgemm(Rt, A_)
+        gflops += sg.plan(T, R).info()["flops"]
+        A_ = sg.spgemm(T, R)
+    out["amg_galerkin_128cubed_3levels"] = {"graph_ms": round(tg * 1e3, 3), "plain_ms": round(tp * 1e3, 3),
+                                            "speedup": round(tp / tg, 3), "flops": int(gflops),
+                                            "gflops_graph": round(2 * gflops / tg / 1e9, 3)}
+    return out
 
 
 def run_e2e(args, A, sg, torch, dev, dP):
@@ -370,6 +443,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-paths", action="store_true",
+                    help="skip the split / batched / AMG comparisons")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

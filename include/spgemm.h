@@ -172,6 +172,66 @@ spgemm_status spgemm_plan_device(int32_t count, const spgemm_csr* A, const spgem
 spgemm_status spgemm_execute(spgemm_plan_t plan, void* ws, size_t ws_bytes, int64_t* rowptrC,
                              int64_t capacity, void* colC, void* valC);
 
+/* ---- learned sizing of C (not in the paper: an addition to the method) ----
+ * A small MLP predicts nnz(C(i,:)) from row features: x = log2(1 + .) of
+ * flops_i, |A(i,:)|, max_k |B(k,:)|, n, flops_i / |A(i,:)|, min(flops_i, n);
+ * layers F -> 32 -> 32 -> 1 with ReLU, float32.  Parameters are one device
+ * float array of spgemm_sizer_param_count(F) entries: W1 (32 x F, row-major),
+ * b1 (32), W2 (32 x 32, row-major), b2 (32), w3 (32), b3 (1).  The target the
+ * network is trained on is log2(1 + nnz(C(i,:))) from the exact symbolic
+ * phase. */
+int32_t spgemm_sizer_param_count(int32_t features);
+/* y[s] = MLP(X[s*F .. s*F+F)) for N samples (device arrays).  No wait. */
+spgemm_status spgemm_sizer_forward(const float* X, int64_t N, int32_t F, const float* params,
+                                   float* y, void* stream);
+/* Gradient of 0.5 * mean_s (MLP(X_s) - T_s)^2 over all N samples into grad
+ * (param_count floats) and the loss into *loss (device).  No wait. */
+spgemm_status spgemm_sizer_grad(const float* X, const float* T, int64_t N, int32_t F,
+                                const float* params, float* grad, float* loss, void* stream);
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on mini-batches of
+ * `batch` consecutive entries of `order` (a permutation of 0..N-1, device
+ * int64), updating params, adam_m, adam_v (zero-initialised by the caller);
+ * grad is scratch (param_count floats); loss_trace[t] receives the batch loss
+ * of step t (device).  No wait. */
+spgemm_status spgemm_sizer_train(const float* X, const float* T, const int64_t* order, int64_t N,
+                                 int32_t F, float* params, float* adam_m, float* adam_v,
+                                 float* grad, int32_t steps, int32_t batch, float lr,
+                                 float* loss_trace, void* stream);
+/* Row features (F = 6, device float [rows x 6]) of a plan's rows, the
+ * predictor's input, for building training sets.  No wait. */
+spgemm_status spgemm_row_features(spgemm_plan_t plan, float* X);
+
+/* Device allocation callback: returns `bytes` (>= 256-byte aligned) of
+ * device memory owned by the caller, or NULL. */
+typedef void* (*spgemm_alloc_fn)(size_t bytes, void* ctx);
+
+typedef struct {
+    int64_t nrows, ncols;
+    int64_t nnz;           /* entries of col/val */
+    int64_t* rowptr;       /* row i starts at rowptr[i] ... */
+    int64_t* rowend;       /* ... and ends at rowend[i] (slots), or NULL: plain CSR */
+    void* col;
+    void* val;
+    int64_t slot_total;    /* sum of the predicted slots */
+    int64_t overflow_rows; /* rows that did not fit their slot (re-run exactly) */
+    int64_t total_flops;
+} spgemm_learned_result;
+
+/* spgemm_learned_multiply -- C = A.B with the symbolic phase of rows of at
+ * most dense_min_flops products replaced by the predictor (params, plus
+ * `margin` in log2 units of safety): those rows are multiplied straight into
+ * predicted slots; rows that overflow are listed and multiplied again by the
+ * exact two-phase path; dense rows keep their exact bitmap count.  Row
+ * contents equal spgemm_symbolic + spgemm_numeric bit for bit.  With no
+ * overflow, C is returned as slots (rowptr/rowend, gaps allowed); otherwise
+ * as a plain compacted CSR.  All device memory comes from `alloc`; the call
+ * waits for the stream (it reads sizes back three or four times).  Single
+ * product; A may be a view (rowend). */
+spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
+                                      const spgemm_opts* opts, const float* params, float margin,
+                                      void* stream, spgemm_alloc_fn alloc, void* ctx,
+                                      spgemm_learned_result* out);
+
 /* Statistics of a plan (host call, no device work). */
 spgemm_status spgemm_plan_info(spgemm_plan_t plan, spgemm_info* info);
 

@@ -107,18 +107,19 @@ size_t plan_workspace_bytes(int nprod, long long R) {
     return align_up(sizeof(DevCounters)) + align_up((size_t)nprod * sizeof(ProdDesc)) +
            2 * align_up((size_t)(nprod + 1) * sizeof(long long)) +
            align_up((size_t)R * sizeof(int64_t)) + align_up((size_t)R) +
-           align_up((size_t)R * sizeof(int32_t));
+           align_up((size_t)R * sizeof(int32_t)) + align_up((size_t)R * sizeof(int64_t));
 }
 
 }  // namespace sg
 
-namespace {
+namespace sg {
 
 // Checks and records a batch of products; shared by spgemm_plan,
 // spgemm_batch_plan and spgemm_plan_device.
 spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
                         const spgemm_opts* opts, void* stream, void* plan_ws, size_t plan_ws_bytes,
-                        bool device_sized, spgemm_plan_t* plan_out) {
+                        bool device_sized, spgemm_plan_t* plan_out, const float* sizer_params,
+                        float sizer_margin) {
     g_last_error.clear();
     if (!plan_out) return fail(SPGEMM_ERR_INVALID_ARG, "plan output pointer is NULL");
     *plan_out = nullptr;
@@ -176,6 +177,8 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->nprod = count;
     P->R = R;
     P->device_sized = device_sized;
+    P->prm = sizer_params;
+    P->margin = sizer_margin;
     P->dense_min = o.dense_min_flops ? o.dense_min_flops : 1024;
     P->sm_count = device_sm_count(&P->smem_optin);
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
@@ -242,6 +245,8 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->cls = P->pws + off;
     off += align_up((size_t)R);
     P->rows = (int32_t*)(P->pws + off);
+    off += align_up((size_t)R * sizeof(int32_t));
+    P->cap = (int64_t*)(P->pws + off);
 
     cudaStream_t s = P->stream;
     cudaError_t e = cudaMemcpyAsync(P->d_descs, P->descs.data(), count * sizeof(sg::ProdDesc),
@@ -358,7 +363,11 @@ cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long 
     }
 }
 
-}  // namespace
+}  // namespace sg
+
+using sg::make_plan;
+using sg::check_ws;
+using sg::run_numeric;
 
 extern "C" {
 
@@ -380,19 +389,21 @@ size_t spgemm_batch_plan_workspace_size(int32_t count, const spgemm_csr* A) {
 spgemm_status spgemm_plan(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
                           void* stream, void* plan_ws, size_t plan_ws_bytes,
                           spgemm_plan_t* plan_out) {
-    return make_plan(1, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out);
+    return make_plan(1, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out, nullptr, 0.f);
 }
 
 spgemm_status spgemm_batch_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
                                 const spgemm_opts* opts, void* stream, void* plan_ws,
                                 size_t plan_ws_bytes, spgemm_plan_t* plan_out) {
-    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out);
+    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, false, plan_out, nullptr,
+                     0.f);
 }
 
 spgemm_status spgemm_plan_device(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
                                  const spgemm_opts* opts, void* stream, void* plan_ws,
                                  size_t plan_ws_bytes, spgemm_plan_t* plan_out) {
-    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, true, plan_out);
+    return make_plan(count, A, B, opts, stream, plan_ws, plan_ws_bytes, true, plan_out, nullptr,
+                     0.f);
 }
 
 spgemm_status spgemm_plan_info(spgemm_plan_t P, spgemm_info* info) {

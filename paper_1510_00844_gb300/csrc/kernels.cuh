@@ -163,14 +163,27 @@ __device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* r
 // One warp per global row: flops_i, its class, per-class counts, total and
 // max flops, longest dense row; a product whose dense rows need more columns
 // than the shared-memory bitmap holds is flagged.
+// Learned sizing (not in the paper): when `prm` is given, the warp also
+// evaluates the row-size predictor on the row's features (one lane per hidden
+// unit), writes the predicted capacity cap_out[r] = clamp(2^(y + margin) - 1,
+// max_k |B(k,:)|, min(flops, n)), and bins rows of at most dense_min products
+// by that capacity instead of by their flops.
+constexpr int kSizerF = 6;
+
 template <class IT>
 __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
                                const long long* __restrict__ rb, int nprod, long long max_dense_n,
                                int dense_min, int64_t* __restrict__ flops_out,
-                               unsigned char* __restrict__ cls_out, DevCounters* cnt) {
+                               unsigned char* __restrict__ cls_out, DevCounters* cnt,
+                               const float* __restrict__ prm, float margin,
+                               int64_t* __restrict__ cap_out) {
     __shared__ unsigned long long hist[kNumClasses];
     __shared__ unsigned long long blk_total, blk_max, blk_dlen;
     __shared__ int blk_unsup;
+    __shared__ float sp[32 * kSizerF + 32 + 32 * 32 + 32 + 32 + 1];
+    if (prm)
+        for (int q = threadIdx.x; q < 32 * kSizerF + 32 + 32 * 32 + 32 + 32 + 1; q += blockDim.x)
+            sp[q] = prm[q];
     for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) hist[t] = 0;
     if (threadIdx.x == 0) {
         blk_total = 0;
@@ -185,15 +198,49 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
     unsigned long long my_total = 0, my_max = 0;
     for (long long r = warp; r < R; r += nwarps) {
         const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
-        long long f = 0;
+        long long f = 0, mx = 0;
         for (long long p = c.a0 + lane; p < c.a1; p += 32) {
             long long k = (long long)c.ciA[p];
-            f += c.rpB[k + 1] - c.rpB[k];
+            const long long len = c.rpB[k + 1] - c.rpB[k];
+            f += len;
+            mx = len > mx ? len : mx;
         }
         f = warp_sum(f);
+        mx = warp_max(mx);
+        long long cap = 0;
+        if (prm && f > 0) {
+            const long long d = c.a1 - c.a0;
+            const long long ub = f < c.n ? f : c.n;
+            float x[kSizerF];
+            x[0] = log2f(1.f + (float)f);
+            x[1] = log2f(1.f + (float)d);
+            x[2] = log2f(1.f + (float)mx);
+            x[3] = log2f(1.f + (float)c.n);
+            x[4] = log2f(1.f + (float)f / (float)d);
+            x[5] = log2f(1.f + (float)ub);
+            const float* W1 = sp;
+            const float* b1 = W1 + 32 * kSizerF;
+            const float* W2 = b1 + 32;
+            const float* b2 = W2 + 32 * 32;
+            const float* w3 = b2 + 32;
+            float z = b1[lane];
+            for (int q = 0; q < kSizerF; ++q) z = __fadd_rn(z, __fmul_rn(W1[lane * kSizerF + q], x[q]));
+            const float h1 = z > 0.f ? z : 0.f;
+            float z2 = b2[lane];
+            for (int k = 0; k < 32; ++k)
+                z2 = __fadd_rn(z2, __fmul_rn(W2[lane * 32 + k], __shfl_sync(kFull, h1, k)));
+            const float h2 = z2 > 0.f ? z2 : 0.f;
+            const float y = warp_sum(__fmul_rn(w3[lane], h2)) + w3[32];
+            const float est = exp2f(y + margin) - 1.f;
+            cap = est >= (float)ub ? ub : (long long)ceilf(est > 0.f ? est : 0.f);
+            if (cap < mx) cap = mx;
+            if (cap > ub) cap = ub;
+        }
         if (lane == 0) {
             flops_out[r] = f;
-            const int cl = row_class(f, dense_min);
+            if (cap_out) cap_out[r] = prm ? cap : f;
+            int cl = row_class(f, dense_min);
+            if (prm && cl > kClassEmpty && cl < kClassDense0) cl = row_class(cap > 0 ? cap : 1, dense_min);
             cls_out[r] = (unsigned char)cl;
             if (cl >= kClassDense0) {
                 if (c.n > max_dense_n) blk_unsup = 1;
@@ -216,6 +263,40 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
         atomicMax(&cnt->max_flops, blk_max);
         atomicMax(&cnt->max_dense_len, blk_dlen);
         if (blk_unsup) atomicExch(&cnt->unsupported, 1);
+    }
+}
+
+// Features of every global row for the row-size predictor (log2(1 + .) of
+// flops, |A(i,:)|, max_k |B(k,:)|, n, flops/|A(i,:)|, min(flops, n)).
+template <class IT>
+__global__ void row_features_kernel(long long R, const ProdDesc* __restrict__ D,
+                                    const long long* __restrict__ rb, int nprod,
+                                    float* __restrict__ X) {
+    const int lane = lane_id();
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = warp; r < R; r += nwarps) {
+        const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
+        long long f = 0, mx = 0;
+        for (long long p = c.a0 + lane; p < c.a1; p += 32) {
+            long long k = (long long)c.ciA[p];
+            const long long len = c.rpB[k + 1] - c.rpB[k];
+            f += len;
+            mx = len > mx ? len : mx;
+        }
+        f = warp_sum(f);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            const long long d = c.a1 - c.a0;
+            const long long ub = f < c.n ? f : c.n;
+            float* x = X + r * kSizerF;
+            x[0] = log2f(1.f + (float)f);
+            x[1] = log2f(1.f + (float)d);
+            x[2] = log2f(1.f + (float)mx);
+            x[3] = log2f(1.f + (float)c.n);
+            x[4] = log2f(1.f + (d > 0 ? (float)f / (float)d : 0.f));
+            x[5] = log2f(1.f + (float)ub);
+        }
     }
 }
 
@@ -475,7 +556,9 @@ __global__ void __launch_bounds__(WARPS * 32)
     numeric_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
                         int cls, const int64_t* __restrict__ rpC, long long cap,
-                        IT* __restrict__ ciC, V* __restrict__ vC, int* err) {
+                        IT* __restrict__ ciC, V* __restrict__ vC, int* err,
+                        int64_t* __restrict__ rowend, int32_t* __restrict__ overflow,
+                        unsigned* overflow_count) {
     using K = typename KeyT<IT>::type;
     constexpr int T = 1 << LOG2T;
     constexpr bool HV = VOps<V>::has_val;
@@ -488,6 +571,13 @@ __global__ void __launch_bounds__(WARPS * 32)
     V* acc = reinterpret_cast<V*>(base);
     K* keys = reinterpret_cast<K*>(base + vbytes);
     int* rcnt_smem = reinterpret_cast<int*>(base + vbytes + sizeof(K) * T);
+    // slot mode (learned sizing): rows go to predicted slots [rpC[r], rpC[r+1]);
+    // a row that does not fit its slot or its table is listed for an exact re-run
+    const bool slot_mode = rowend != nullptr;
+    __shared__ int warp_fail[WARPS];
+    int* fail = slot_mode ? &warp_fail[w] : err;
+    if (lane == 0) warp_fail[w] = 0;
+    __syncwarp();
     for (int s = lane; s < T; s += 32) {
         keys[s] = K(-1);
         if constexpr (HV) acc[s] = VOps<V>::init();
@@ -523,7 +613,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 V v{};
                 if (valid) {
                     bool is_new;
-                    slot = hash_insert<LOG2T>(keys, (K)ciB[q], is_new, err);
+                    slot = hash_insert<LOG2T>(keys, (K)ciB[q], is_new, fail);
                     v = VOps<V>::mul(ae, load_val(vB, q));
                 }
                 valid = valid && slot >= 0;
@@ -533,7 +623,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         // compact occupied slots to the front (ascending slot order)
         const long long out = rpC[r];
-        const int rcnt = (int)(rpC[r + 1] - out);
+        int rcnt = (int)(rpC[r + 1] - out);
         int pos = 0;
         for (int s0 = 0; s0 < T; s0 += 32) {
             K kk = keys[s0 + lane];
@@ -550,7 +640,27 @@ __global__ void __launch_bounds__(WARPS * 32)
             pos += __popc(msk);
             __syncwarp();
         }
-        if (pos != rcnt && lane == 0) atomicExch(err, (int)kDevCountMismatch);
+        if (slot_mode) {
+            __syncwarp();
+            const bool bad = warp_fail[w] != 0 || pos > rcnt;
+            if (bad) {
+                if (lane == 0) {
+                    overflow[atomicAdd(overflow_count, 1u)] = (int32_t)r;
+                    rowend[r] = -1;
+                    warp_fail[w] = 0;
+                }
+                for (int sl = lane; sl < T; sl += 32) {
+                    keys[sl] = K(-1);
+                    if constexpr (HV) acc[sl] = VOps<V>::init();
+                }
+                __syncwarp();
+                continue;
+            }
+            rcnt = pos;
+            if (lane == 0) rowend[r] = out + pos;
+        } else if (pos != rcnt && lane == 0) {
+            atomicExch(err, (int)kDevCountMismatch);
+        }
         if (out + rcnt > cap && lane == 0) atomicExch(err, (int)kDevCapacity);
         const K* sk = keys;
         const V* sv = acc;

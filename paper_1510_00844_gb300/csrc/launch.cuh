@@ -49,7 +49,17 @@ cudaError_t launch_analyze(Plan& P) {
     long long g = grid_for(P.R, 8, P.sm_count, occ);
     count_launches(1);
     k<<<(unsigned)g, 256, 0, P.stream>>>(P.R, P.d_descs, P.rb, P.nprod, P.max_dense_n,
-                                           P.dense_min, P.flops, P.cls, P.cnt);
+                                           P.dense_min, P.flops, P.cls, P.cnt, P.prm, P.margin,
+                                           P.cap);
+    return cudaGetLastError();
+}
+
+template <class IT>
+cudaError_t launch_row_features(Plan& P, float* X) {
+    if (P.R <= 0) return cudaSuccess;
+    long long g = grid_for(P.R, 8, P.sm_count, 8);
+    count_launches(1);
+    row_features_kernel<IT><<<(unsigned)g, 256, 0, P.stream>>>(P.R, P.d_descs, P.rb, P.nprod, X);
     return cudaGetLastError();
 }
 
@@ -141,7 +151,7 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
 
 template <class IT, class V, int LOG2T, int WARPS>
 cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT* colC,
-                         V* valC) {
+                         V* valC, int64_t* rowend, int32_t* overflow, unsigned* overflow_count) {
     using K = typename KeyT<IT>::type;
     const int c = kClassHash0 + bin;
     const long long nrows = (long long)P.class_count[c];
@@ -156,7 +166,8 @@ cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT
     long long g = class_grid(P, nrows, WARPS, occ);
     count_launches(1);
     k<<<(unsigned)g, WARPS * 32, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt, c,
-                                                   rpC, cap, colC, valC, &P.cnt->err);
+                                                   rpC, cap, colC, valC, &P.cnt->err, rowend,
+                                                   overflow, overflow_count);
     return cudaGetLastError();
 }
 
@@ -182,14 +193,15 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
 
 template <class IT, class V>
 cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
-                           void* colC_, void* valC_) {
+                           void* colC_, void* valC_, int64_t* rowend, int32_t* overflow,
+                           unsigned* overflow_count) {
     IT* colC = (IT*)colC_;
     V* valC = (V*)valC_;
     cudaError_t e;
-    if ((e = num_hash_bin<IT, V, 6, 8>(P, 0, rpC, cap, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 8, 8>(P, 1, rpC, cap, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 10, 8>(P, 2, rpC, cap, colC, valC)) != cudaSuccess) return e;
-    if ((e = num_hash_bin<IT, V, 11, 4>(P, 3, rpC, cap, colC, valC)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 6, 8>(P, 0, rpC, cap, colC, valC, rowend, overflow, overflow_count)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 8, 8>(P, 1, rpC, cap, colC, valC, rowend, overflow, overflow_count)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 10, 8>(P, 2, rpC, cap, colC, valC, rowend, overflow, overflow_count)) != cudaSuccess) return e;
+    if ((e = num_hash_bin<IT, V, 11, 4>(P, 3, rpC, cap, colC, valC, rowend, overflow, overflow_count)) != cudaSuccess) return e;
     if (P.device_sized || P.ndense > 0) {
         e = P.W == kDenseW0
                 ? launch_numeric_dense<IT, V, kDenseW0, kDenseWarps0>(P, ws, rpC, cap, colC, valC)
@@ -230,12 +242,17 @@ cudaError_t prepare_numeric(Plan& P) {
     template cudaError_t prepare_numeric<IT, int64_t>(Plan&);                                  \
     template cudaError_t prepare_numeric<IT, NoVal>(Plan&);                                    \
     template cudaError_t launch_numeric<IT, double>(Plan&, unsigned char*, const int64_t*,     \
-                                                    long long, void*, void*);                  \
+                                                    long long, void*, void*, int64_t*,         \
+                                                    int32_t*, unsigned*);                      \
     template cudaError_t launch_numeric<IT, float>(Plan&, unsigned char*, const int64_t*,      \
-                                                   long long, void*, void*);                   \
+                                                   long long, void*, void*, int64_t*,          \
+                                                   int32_t*, unsigned*);                       \
     template cudaError_t launch_numeric<IT, int64_t>(Plan&, unsigned char*, const int64_t*,    \
-                                                     long long, void*, void*);                 \
+                                                     long long, void*, void*, int64_t*,        \
+                                                     int32_t*, unsigned*);                     \
     template cudaError_t launch_numeric<IT, NoVal>(Plan&, unsigned char*, const int64_t*,      \
-                                                   long long, void*, void*);
+                                                   long long, void*, void*, int64_t*,          \
+                                                   int32_t*, unsigned*);                       \
+    template cudaError_t launch_row_features<IT>(Plan&, float*);
 
 }  // namespace sg

@@ -37,6 +37,9 @@ struct spgemm_plan_s {
     int64_t* flops = nullptr;
     unsigned char* cls = nullptr;
     int32_t* rows = nullptr;
+    int64_t* cap = nullptr;          // predicted (learned plans) or flops bound per row
+    const float* prm = nullptr;      // row-size predictor parameters (learned plans)
+    float margin = 0.f;              // log2 safety margin added to the prediction
     // host copies of the row analysis (host-synced plans)
     unsigned long long class_count[sg::kNumClasses] = {};
     long long class_off[sg::kNumClasses + 1] = {};
@@ -67,6 +70,14 @@ struct WsLayout {
 WsLayout workspace_layout(const Plan& P);
 size_t plan_workspace_bytes(int nprod, long long R);
 
+spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
+                        const spgemm_opts* opts, void* stream, void* plan_ws, size_t plan_ws_bytes,
+                        bool device_sized, spgemm_plan_t* plan_out, const float* sizer_params,
+                        float sizer_margin);
+spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes);
+cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long long cap,
+                        void* colC, void* valC);
+
 size_t scan_temp_bytes(long long N);
 cudaError_t launch_exclusive_scan(int64_t* x, long long N, int64_t* temp, cudaStream_t s);
 cudaError_t launch_binning(Plan& P);
@@ -77,6 +88,8 @@ cudaError_t launch_product_rowptr(const Plan& P, const int64_t* g, int64_t* out)
 template <class IT>
 cudaError_t launch_analyze(Plan& P);
 template <class IT>
+cudaError_t launch_row_features(Plan& P, float* X);
+template <class IT>
 cudaError_t launch_validate(const spgemm_csr& M, int* err, int sm_count, cudaStream_t s);
 template <class IT>
 cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt);
@@ -84,7 +97,8 @@ template <class IT, class V>
 cudaError_t prepare_numeric(Plan& P);
 template <class IT, class V>
 cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
-                           void* colC, void* valC);
+                           void* colC, void* valC, int64_t* rowend = nullptr,
+                           int32_t* overflow = nullptr, unsigned* overflow_count = nullptr);
 cudaError_t launch_merge(int c, const spgemm_csr* parts, int vt, long long m, long long n,
                          int sm_count, cudaStream_t s, bool numeric, int64_t* rowcnt,
                          const int64_t* rpC, void* colC, void* valC, int* err);

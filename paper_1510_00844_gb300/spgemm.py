@@ -72,6 +72,12 @@ def _load():
         "spgemm_execute": (st, [P, P, S, P, I64_, P, P]),
         "spgemm_batch_rowptrs": (st, [P, P, P]),
         "spgemm_transpose_workspace_size": (S, [P]),
+        "spgemm_sizer_param_count": (I32_, [I32_]),
+        "spgemm_sizer_forward": (st, [P, I64_, I32_, P, P, P]),
+        "spgemm_sizer_grad": (st, [P, P, I64_, I32_, P, P, P, P]),
+        "spgemm_sizer_train": (st, [P, P, P, I64_, I32_, P, P, P, P, I32_, I32_, ctypes.c_float, P, P]),
+        "spgemm_row_features": (st, [P, P]),
+        "spgemm_learned_multiply": (st, [P, P, P, P, ctypes.c_float, P, P, P, P]),
         "spgemm_transpose": (st, [P, P, P, S, P, P, P]),
         "spgemm_plan_info": (st, [P, P]),
         "spgemm_workspace_size": (st, [P, P]),
@@ -369,6 +375,141 @@ def transpose(A: DeviceCSR, stream=None) -> DeviceCSR:
                                  ctypes.c_void_p(col.data_ptr()) if A.nnz else None,
                                  None if val is None or A.nnz == 0 else ctypes.c_void_p(val.data_ptr())))
     return DeviceCSR(A.ncols, A.nrows, rp, col, val)
+
+
+# ------------------------------------------------------------ learned sizing
+SIZER_F = 6
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class _LearnedResult(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("rowend", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("slot_total", ctypes.c_int64), ("overflow_rows", ctypes.c_int64),
+                ("total_flops", ctypes.c_int64)]
+
+
+def sizer_param_count(F: int = SIZER_F) -> int:
+    return int(_lib.spgemm_sizer_param_count(F))
+
+
+def sizer_forward(X: torch.Tensor, params: torch.Tensor, stream=None) -> torch.Tensor:
+    N, F = X.shape
+    y = torch.empty(N, dtype=torch.float32, device=X.device)
+    _check(_lib.spgemm_sizer_forward(ctypes.c_void_p(X.data_ptr()), N, F,
+                                     ctypes.c_void_p(params.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()), _stream(stream)))
+    return y
+
+
+def sizer_grad(X: torch.Tensor, T: torch.Tensor, params: torch.Tensor, stream=None):
+    N, F = X.shape
+    g = torch.empty(sizer_param_count(F), dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(_lib.spgemm_sizer_grad(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                  N, F, ctypes.c_void_p(params.data_ptr()),
+                                  ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                  _stream(stream)))
+    return g, loss
+
+
+def sizer_init(F: int = SIZER_F, seed: int = 0, device="cuda") -> torch.Tensor:
+    """He-style random initial parameters (seeded, drawn on the host)."""
+    rng = np.random.default_rng(seed)
+    H = 32
+    parts = [rng.normal(0, np.sqrt(2.0 / F), H * F), np.zeros(H),
+             rng.normal(0, np.sqrt(2.0 / H), H * H), np.zeros(H),
+             rng.normal(0, np.sqrt(1.0 / H), H), np.zeros(1)]
+    return torch.tensor(np.concatenate(parts), dtype=torch.float32, device=device)
+
+
+def sizer_train(X: torch.Tensor, T: torch.Tensor, params: torch.Tensor, steps: int, batch: int,
+                lr: float, seed: int = 0, stream=None) -> torch.Tensor:
+    """Adam steps on (X, T) in place on params; returns the per-step loss."""
+    N, F = X.shape
+    order = torch.from_numpy(np.random.default_rng(seed).permutation(N).astype(np.int64)).to(X.device)
+    P = sizer_param_count(F)
+    m = torch.zeros(P, dtype=torch.float32, device=X.device)
+    v = torch.zeros(P, dtype=torch.float32, device=X.device)
+    g = torch.empty(P, dtype=torch.float32, device=X.device)
+    trace = torch.empty(max(steps, 1), dtype=torch.float32, device=X.device)
+    _check(_lib.spgemm_sizer_train(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                   ctypes.c_void_p(order.data_ptr()), N, F,
+                                   ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                                   ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                   steps, batch, ctypes.c_float(lr),
+                                   ctypes.c_void_p(trace.data_ptr()), _stream(stream)))
+    return trace[:steps]
+
+
+def row_features(p: Plan) -> torch.Tensor:
+    X = torch.empty((getattr(p, "R", p.A.nrows), SIZER_F), dtype=torch.float32, device=p.device)
+    _check(_lib.spgemm_row_features(p._h, ctypes.c_void_p(X.data_ptr())))
+    return X
+
+
+def sizer_training_set(pairs, stream=None):
+    """(features, log2(1 + nnz(C(i,:)))) of every non-empty row of the given
+    products, the targets from the exact symbolic phase."""
+    Xs, Ts = [], []
+    for A, B in pairs:
+        p = plan(A, B, stream=stream)
+        X = row_features(p)
+        rp, _ = symbolic(p)
+        cnt = (rp[1:] - rp[:-1]).to(torch.float32)
+        keep = X[:, 0] > 0
+        Xs.append(X[keep])
+        Ts.append(torch.log2(1.0 + cnt[keep]))
+        p.close()
+    return torch.cat(Xs), torch.cat(Ts)
+
+
+def learned_multiply(A: DeviceCSR, B: DeviceCSR, params: torch.Tensor, margin: float = 0.25,
+                     semiring: int = PLUS_TIMES, stream=None, dense_min_flops: int = 0):
+    """C = A.B with learned sizing (spgemm_learned_multiply).  Returns
+    (C, stats); C carries rowend when it is returned as slots."""
+    keep = []
+    dev = A.rowptr.device
+
+    def alloc(nbytes, ctx):
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=dev)
+        keep.append(t)
+        return t.data_ptr()
+
+    cb = _ALLOC_FN(alloc)
+    cA, cB = _csr(A), _csr(B)
+    opts = _Opts(semiring, 0, 0, dense_min_flops, 0)
+    res = _LearnedResult()
+    _check(_lib.spgemm_learned_multiply(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(opts),
+                                        ctypes.c_void_p(params.data_ptr()), ctypes.c_float(margin),
+                                        _stream(stream), cb, None, ctypes.byref(res)))
+    by_ptr = {t.data_ptr(): t for t in keep}
+
+    def view(ptr, dtype, count):
+        if count == 0:
+            return torch.empty(0, dtype=dtype, device=dev)
+        t = by_ptr[ptr]
+        return t[: count * torch.empty(0, dtype=dtype).element_size()].view(dtype)
+
+    m = res.nrows
+    rowptr = view(res.rowptr, torch.int64, m + 1)
+    rowend = view(res.rowend, torch.int64, m) if res.rowend else None
+    col = view(res.col, A.col.dtype, res.nnz)
+    pattern = semiring == OR_AND or A.val is None
+    val = None if pattern else view(res.val, A.val.dtype, res.nnz)
+    C = DeviceCSR(m, res.ncols, rowptr, col, val, rowend=rowend)
+    stats = {"slot_total": res.slot_total, "overflow_rows": res.overflow_rows,
+             "flops": res.total_flops, "slots": res.rowend is not None}
+    C._keep = keep
+    return C, stats
+
+
+def compact(C: DeviceCSR) -> DeviceCSR:
+    """A plain CSR copy of a CSR view (rowend given): rows packed."""
+    if C.rowend is None:
+        return C
+    return merge([DeviceCSR(C.nrows, C.ncols, C.rowptr, C.col, C.val, rowend=C.rowend)])
 
 
 def kslice_bounds(A: DeviceCSR, c: int, stream=None) -> torch.Tensor:
