@@ -274,6 +274,21 @@ size_t spgemm_transpose_workspace_size(const spgemm_csr* A);
 spgemm_status spgemm_transpose(const spgemm_csr* A, void* stream, void* ws, size_t ws_bytes,
                                int64_t* rowptrT, void* colT, void* valT);
 
+/* ---- Markov-clustering epilogue (MCL expansion = squaring, Sec. 5.3) ----
+ * On M^T in CSR (float64; rowend views allowed): keep entries >= threshold,
+ * divide each row by the sum of its kept entries (rows that lose every entry
+ * stay empty).  Count pass writes rowptrP (int64[m+1]) and nnz to the host
+ * (waits); fill pass writes colP (index type of C) / valP (float64).  `ws` is
+ * spgemm_mcl_workspace_size(m) bytes, 256-byte aligned, kept between the two
+ * calls. */
+size_t spgemm_mcl_workspace_size(int64_t m);
+spgemm_status spgemm_mcl_prune_count(const spgemm_csr* C, double threshold, void* stream,
+                                     void* ws, size_t ws_bytes, int64_t* rowptrP,
+                                     int64_t* nnz_host);
+spgemm_status spgemm_mcl_prune_fill(const spgemm_csr* C, double threshold, void* stream, void* ws,
+                                    size_t ws_bytes, const int64_t* rowptrP, void* colP,
+                                    double* valP);
+
 /* ---- k-slices and their merge (Alg. 2 split of the inner dimension;
  *      multiway merge with duplicate reduction, Sec. 4.3) ---- */
 

@@ -73,6 +73,9 @@ def _load():
         "spgemm_batch_rowptrs": (st, [P, P, P]),
         "spgemm_transpose_workspace_size": (S, [P]),
         "spgemm_sizer_param_count": (I32_, [I32_]),
+        "spgemm_mcl_workspace_size": (S, [I64_]),
+        "spgemm_mcl_prune_count": (st, [P, ctypes.c_double, P, P, S, P, P]),
+        "spgemm_mcl_prune_fill": (st, [P, ctypes.c_double, P, P, S, P, P, P]),
         "spgemm_sizer_forward": (st, [P, I64_, I32_, P, P, P]),
         "spgemm_sizer_grad": (st, [P, P, I64_, I32_, P, P, P, P]),
         "spgemm_sizer_train": (st, [P, P, P, I64_, I32_, P, P, P, P, I32_, I32_, ctypes.c_float, P, P]),
@@ -375,6 +378,38 @@ def transpose(A: DeviceCSR, stream=None) -> DeviceCSR:
                                  ctypes.c_void_p(col.data_ptr()) if A.nnz else None,
                                  None if val is None or A.nnz == 0 else ctypes.c_void_p(val.data_ptr())))
     return DeviceCSR(A.ncols, A.nrows, rp, col, val)
+
+
+# ------------------------------------------------------------ MCL epilogue
+def mcl_prune(C: DeviceCSR, threshold: float = 1e-4, stream=None) -> DeviceCSR:
+    """Drop entries below threshold, renormalise rows (float64)."""
+    cC = _csr(C)
+    dev = C.rowptr.device
+    ws = _workspace(_lib.spgemm_mcl_workspace_size(C.nrows), dev)
+    rp = torch.empty(C.nrows + 1, dtype=torch.int64, device=dev)
+    nnz = ctypes.c_int64()
+    _check(_lib.spgemm_mcl_prune_count(ctypes.byref(cC), ctypes.c_double(threshold), _stream(stream),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       ctypes.c_void_p(rp.data_ptr()), ctypes.byref(nnz)))
+    col = torch.empty(nnz.value, dtype=C.col.dtype, device=dev)
+    val = torch.empty(nnz.value, dtype=torch.float64, device=dev)
+    _check(_lib.spgemm_mcl_prune_fill(ctypes.byref(cC), ctypes.c_double(threshold), _stream(stream),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      ctypes.c_void_p(rp.data_ptr()),
+                                      ctypes.c_void_p(col.data_ptr()) if nnz.value else None,
+                                      ctypes.c_void_p(val.data_ptr()) if nnz.value else None))
+    return DeviceCSR(C.nrows, C.ncols, rp, col, val)
+
+
+def mcl_step(M: DeviceCSR, threshold: float = 1e-4, params: Optional[torch.Tensor] = None,
+             margin: float = 0.25, stream=None) -> DeviceCSR:
+    """One MCL expansion on M^T in CSR: (M M)^T = M^T M^T, then the epilogue.
+    With params the product uses learned sizing."""
+    if params is None:
+        C = spgemm(M, M, stream=stream)
+    else:
+        C, _ = learned_multiply(M, M, params, margin, stream=stream)
+    return mcl_prune(C, threshold, stream)
 
 
 # ------------------------------------------------------------ learned sizing
