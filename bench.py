@@ -218,6 +218,8 @@ def run_ours(args):
     traffic = profiled_traffic()
 
     paths = run_paths(args, A, dA, sg, torch) if (rank == 0 and world == 1 and not args.no_paths) else None
+    if paths is not None and not args.no_learned:
+        paths["learned"] = run_learned(args, sg, torch)
     e2e = (run_e2e(args, A, sg, torch, dev, dP if world == 1 else None)
            if rank == 0 and not args.no_e2e else None)
     cpu = run_cpu_baseline(A) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -317,6 +319,106 @@ def run_paths(args, A, dA, sg, torch):
     out["amg_galerkin_128cubed_3levels"] = {"graph_ms": round(tg * 1e3, 3), "plain_ms": round(tp * 1e3, 3),
                                             "speedup": round(tp / tg, 3), "flops": int(gflops),
                                             "gflops_graph": round(2 * gflops / tg / 1e9, 3)}
+    return out
+
+
+def _checksum(torch, C):
+    """Order-sensitive int64 digest of a CSR (rows, columns, value bits)."""
+    rp = C.rowptr[: C.nrows + 1]
+    cnt = (rp[1:] - rp[:-1]).to(torch.int64)
+    h = int((cnt * torch.arange(1, C.nrows + 1, device=cnt.device)).sum().item())
+    pos = torch.arange(C.col.numel(), device=cnt.device, dtype=torch.int64)
+    h ^= int(((C.col.to(torch.int64) + 7) * (pos % 1000003 + 1)).sum().item())
+    if C.val is not None:
+        bits = C.val.view(torch.int64) if C.val.dtype == torch.float64 else C.val.to(torch.int64)
+        h ^= int((bits * (pos % 999983 + 3)).sum().item())
+    return h
+
+
+def train_sizer(sg, torch, inputs):
+    """Predictor trained on the GPU on exact symbolic outputs of R-MAT scales
+    14-16 and ER matrices (the training recipe of the learned-sizing row)."""
+    pairs = [inputs.rmat(s, seed=500 + s) for s in (14, 15, 16)]
+    pairs += [inputs.er_column_regular(1 << 15, d, 600 + d) for d in (8, 16)]
+    dev = [(sg.to_device(A), sg.to_device(A)) for A in pairs]
+    X, T = sg.sizer_training_set(dev)
+    params = sg.sizer_init(seed=7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trace = sg.sizer_train(X, T, params, steps=1500, batch=4096, lr=3e-3, seed=8)
+    torch.cuda.synchronize()
+    tt = time.perf_counter() - t0
+    y = sg.sizer_forward(X, params)
+    rmse = float(((y - T) ** 2).mean().sqrt())
+    return params, {"samples": int(X.shape[0]), "steps": 1500, "train_s": round(tt, 3),
+                    "final_loss": round(float(trace[-50:].mean()), 5), "rmse_log2": round(rmse, 4)}
+
+
+def run_learned(args, sg, torch):
+    """Learned sizing vs the exact two-phase path: R-MAT scale 20 squaring in
+    row panels (C does not fit HBM; each panel is reduced to a checksum), and
+    five MCL steps on a column-stochastic R-MAT scale 20 matrix."""
+    from paper_1510_00844_gb300 import inputs
+    params, train = train_sizer(sg, torch, inputs)
+    out = {"sizer": train}
+    margin = 0.35
+    A = inputs.rmat(20)
+    dA = sg.to_device(A)
+    npan = 16
+    bounds = [((A.nrows * p) // npan, (A.nrows * (p + 1)) // npan) for p in range(npan)]
+    views = [sg.DeviceCSR(b - a, A.ncols, dA.rowptr[a:b], dA.col, dA.val, rowend=dA.rowptr[a + 1:b + 1])
+             for a, b in bounds]
+    fl = sum(sg.plan(v, dA).info()["flops"] for v in views)
+    times = {"plain": 0.0, "learned": 0.0}
+    same = True
+    overflow = 0
+    for v in views:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C = sg.spgemm(v, dA)
+        torch.cuda.synchronize()
+        times["plain"] += time.perf_counter() - t0
+        h1 = _checksum(torch, C)
+        del C
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        L, st = sg.learned_multiply(v, dA, params, margin)
+        torch.cuda.synchronize()
+        times["learned"] += time.perf_counter() - t0
+        overflow += st["overflow_rows"]
+        Lc = sg.compact(L)
+        same = same and _checksum(torch, Lc) == h1
+        del L, Lc
+        torch.cuda.empty_cache()
+    out["rmat20_squared_panels16"] = {
+        "plain_ms": round(times["plain"] * 1e3, 1), "learned_ms": round(times["learned"] * 1e3, 1),
+        "speedup": round(times["plain"] / times["learned"], 3), "flops": int(fl),
+        "gflops_plain": round(2 * fl / times["plain"] / 1e9, 2),
+        "gflops_learned": round(2 * fl / times["learned"] / 1e9, 2),
+        "overflow_rows": int(overflow), "bit_identical": bool(same)}
+    del views, dA, A
+    torch.cuda.empty_cache()
+    print("learned rmat20:", json.dumps(out), flush=True, file=sys.stderr)
+    if not args.mcl:
+        return out
+    M = inputs.mcl_transition(20)
+    dM = sg.to_device(M)
+    res = {}
+    for mode in ("plain", "learned"):
+        X = dM
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            X = sg.mcl_step(X, 1e-4, params=params if mode == "learned" else None, margin=margin)
+        torch.cuda.synchronize()
+        res[mode] = (time.perf_counter() - t0, _checksum(torch, X), X.nnz)
+        del X
+        torch.cuda.empty_cache()
+    out["mcl5_rmat20"] = {"plain_ms": round(res["plain"][0] * 1e3, 1),
+                          "learned_ms": round(res["learned"][0] * 1e3, 1),
+                          "speedup": round(res["plain"][0] / res["learned"][0], 3),
+                          "nnz_final": int(res["plain"][2]),
+                          "bit_identical": res["plain"][1] == res["learned"][1]}
     return out
 
 
@@ -443,6 +545,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-sizing comparison (R-MAT 20 squaring)")
+    ap.add_argument("--mcl", action="store_true",
+                    help="add five MCL steps on R-MAT 20 to the learned-sizing leg (about 9 min)")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the split / batched / AMG comparisons")
     args = ap.parse_args()

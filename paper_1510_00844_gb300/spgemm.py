@@ -402,14 +402,30 @@ def mcl_prune(C: DeviceCSR, threshold: float = 1e-4, stream=None) -> DeviceCSR:
 
 
 def mcl_step(M: DeviceCSR, threshold: float = 1e-4, params: Optional[torch.Tensor] = None,
-             margin: float = 0.25, stream=None) -> DeviceCSR:
+             margin: float = 0.25, stream=None, panel_bytes: float = 32e9) -> DeviceCSR:
     """One MCL expansion on M^T in CSR: (M M)^T = M^T M^T, then the epilogue.
-    With params the product uses learned sizing."""
-    if params is None:
-        C = spgemm(M, M, stream=stream)
-    else:
-        C, _ = learned_multiply(M, M, params, margin, stream=stream)
-    return mcl_prune(C, threshold, stream)
+    With params the product uses learned sizing.  When the unpruned product
+    could exceed panel_bytes (flops bound x 12 bytes), rows are processed in
+    panels, each pruned before the next is formed."""
+    fl = plan(M, M, stream=stream).info()["flops"]
+    npan = max(1, int(np.ceil(fl * (M.col.element_size() + 8) / panel_bytes)))
+    parts = []
+    for p in range(npan):
+        a, b = (M.nrows * p) // npan, (M.nrows * (p + 1)) // npan
+        V = M if npan == 1 else DeviceCSR(b - a, M.ncols, M.rowptr[a:b], M.col, M.val,
+                                          rowend=M.rowptr[a + 1:b + 1])
+        if params is None:
+            C = spgemm(V, M, stream=stream)
+        else:
+            C, _ = learned_multiply(V, M, params, margin, stream=stream)
+        parts.append(mcl_prune(C, threshold, stream))
+        del C
+    if npan == 1:
+        return parts[0]
+    offs = np.cumsum([0] + [P.nnz for P in parts])
+    rowptr = torch.cat([parts[0].rowptr[:1]] + [P.rowptr[1:] + int(o) for P, o in zip(parts, offs)])
+    return DeviceCSR(M.nrows, M.ncols, rowptr, torch.cat([P.col for P in parts]),
+                     torch.cat([P.val for P in parts]))
 
 
 # ------------------------------------------------------------ learned sizing
