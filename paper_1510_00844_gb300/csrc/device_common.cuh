@@ -29,6 +29,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+__device__ __forceinline__ unsigned lanemask_le() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 template <class T>
@@ -64,7 +70,9 @@ __device__ __forceinline__ T warp_max(T x) {
 // intrinsics, so no multiply-add is ever fused: every product is rounded
 // before it joins the running sum, as in the plain definition.  Sums start
 // from -0.0, the identity of IEEE addition (-0 + x == x for every x,
-// including +0 and -0), so the first product enters the sum unchanged.
+// including +0 and -0), so the first product enters the sum unchanged.  (On
+// this GPU a fused multiply-add is also slower here than the two separate
+// operations, whose multiply leaves the accumulator's dependency chain.)
 struct NoVal {};
 
 template <class V>

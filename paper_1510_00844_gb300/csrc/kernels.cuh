@@ -31,7 +31,7 @@ constexpr int kClassDense0 = kClassHash0 + kNumHashBins;          // largest-flo
 constexpr int kNumClasses = kClassDense0 + (kDenseMaxLog2 - kDenseMinLog2 + 1);
 constexpr int kSegGrid = 16;
 // Dense chunk configurations (columns per chunk, warps per block): one is
-// chosen per plan (spgemm_opts.reserved[0] = 1 or 2 forces one).
+// chosen per plan (spgemm_opts.dense_chunk forces one).
 constexpr int kDenseW0 = 1024, kDenseWarps0 = 8;
 constexpr int kDenseW1 = 2048, kDenseWarps1 = 4;
 
@@ -720,6 +720,14 @@ struct __align__(16) DenseCursor {
     int next_col;
 };
 
+// One run of a batch in the dense numeric kernel: the flattened product f
+// of the run sits at B position off + f, and is scaled by a = A(i,k).
+template <class V>
+struct __align__(16) DenseRun {
+    long long off;
+    V a;
+};
+
 // runlen[run_base + q] = number of entries from q to the end of q's column
 // chunk (col / W) inside its row of B: the length of the part of B(k,:) that
 // a chunk sweep consumes in one step.  One warp per B row of every product,
@@ -804,9 +812,10 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
     constexpr size_t vbytes = HV ? sizeof(V) * W : 0;
-    unsigned char* base = smem_raw + (size_t)w * (vbytes + W / 8);
+    unsigned char* base = smem_raw + (size_t)w * (vbytes + W / 8 + 32 * sizeof(DenseRun<V>));
     V* acc = reinterpret_cast<V*>(base);
     unsigned* bm = reinterpret_cast<unsigned*>(base + vbytes);
+    DenseRun<V>* runs = reinterpret_cast<DenseRun<V>*>(base + vbytes + W / 8);
     DenseCursor* cursor = arena + ((long long)blockIdx.x * WARPS + w) * arena_stride;
     for (int s = lane; s < W; s += 32)
         if constexpr (HV) acc[s] = VOps<V>::init();
@@ -886,7 +895,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                 DenseCursor cs2{0, 0, 0x7fffffff};
                 if (lane < nb) cs2 = cursor[p - a0];
                 const bool here = lane < nb && (long long)cs2.next_col < c1;
-                if (__ballot_sync(kFull, here) == 0u) continue;
+                const unsigned hmask = __ballot_sync(kFull, here);
+                if (hmask == 0u) continue;
                 // the part of B(k,:) inside this chunk: runlen entries from the cursor
                 int len = 0;
                 V a = VOps<V>::init();
@@ -894,47 +904,66 @@ __global__ void __launch_bounds__(WARPS * 32)
                     len = rlen[cs2.pos];
                     a = load_val(vA, p);
                 }
-                const long long cur = cs2.pos;
                 const int incl = warp_incl_scan(len);
                 const int excl = incl - len;
                 const int total = __shfl_sync(kFull, incl, 31);
-                const int key = lane < nb ? excl : 0x7fffffff;
-                // flattened rounds over the batch's products in ascending k,
-                // four rounds per step so their loads overlap
+                // nonempty runs in k order: run e starts at flattened position
+                // excl_e, its products are B[off_e + f] for f in the run
+                if (here) {
+                    DenseRun<V> re;
+                    re.off = cs2.pos - excl;
+                    re.a = a;
+                    runs[__popc(hmask & lanemask_lt())] = re;
+                }
+                __syncwarp();
+                // flattened rounds of 32 products in ascending k; up to four
+                // rounds per step so their loads overlap.  The run of lane x in
+                // the round starting at w0 is (runs started before w0) + (runs
+                // starting in [w0, w0 + x]) - 1, from an OR of start bits.
+                int started = 0;
                 for (int f0 = 0; f0 < total; f0 += 128) {
+                    const int nsub = min(4, (total - f0 + 31) >> 5);
                     long long jj[4];
                     V bv[4];
                     V av[4];
                     bool vl[4];
-                    bool one_seg[4];
+                    bool multi[4];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int fi = f0 + 32 * t + lane;
-                        int ee = 0;
-#pragma unroll
-                        for (int sb = 16; sb; sb >>= 1) {
-                            int kc = __shfl_sync(kFull, key, ee + sb);
-                            if (kc <= fi) ee += sb;
+                        if (t < nsub) {
+                            const int w0 = f0 + 32 * t;
+                            const unsigned sbit =
+                                (here && excl >= w0 && excl < w0 + 32) ? (1u << (excl - w0)) : 0u;
+                            const unsigned M = __reduce_or_sync(kFull, sbit);
+                            const int e = started + __popc(M & lanemask_le()) - 1;
+                            started += __popc(M);
+                            multi[t] = (M & ~1u) != 0u;
+                            const int fi = w0 + lane;
+                            vl[t] = fi < total;
+                            jj[t] = c0;
+                            bv[t] = V{};
+                            av[t] = V{};
+                            if (vl[t]) {
+                                const DenseRun<V> re = runs[e];
+                                const long long q = re.off + fi;
+                                jj[t] = (long long)ciB[q];
+                                bv[t] = load_val(vB, q);
+                                av[t] = re.a;
+                            }
                         }
-                        const long long qb = __shfl_sync(kFull, cur, ee);
-                        const int ex = __shfl_sync(kFull, excl, ee);
-                        av[t] = shfl_val(a, ee);
-                        vl[t] = fi < total;
-                        one_seg[t] = __shfl_sync(kFull, ee, 0) == __shfl_sync(kFull, ee, 31);
-                        const long long q = qb + (fi - ex);
-                        jj[t] = vl[t] ? (long long)ciB[q] : c0;
-                        bv[t] = vl[t] ? load_val(vB, q) : V{};
                     }
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int slot = (int)(jj[t] - c0);
-                        V v{};
-                        if (vl[t]) {
-                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                            v = VOps<V>::mul(av[t], bv[t]);
+                        if (t < nsub) {
+                            const int slot = (int)(jj[t] - c0);
+                            V v{};
+                            if (vl[t]) {
+                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                                v = VOps<V>::mul(av[t], bv[t]);
+                            }
+                            if (multi[t]) ordered_add(acc, slot, vl[t], v);
+                            else plain_add(acc, slot, vl[t], v);
                         }
-                        if (one_seg[t]) plain_add(acc, slot, vl[t], v);
-                        else ordered_add(acc, slot, vl[t], v);
                     }
                 }
                 if (here) {

@@ -35,10 +35,11 @@ inline long long class_grid(const Plan& P, long long rows_known, int per_block, 
     return grid_for(rows_known, per_block, P.sm_count, occ);
 }
 
-// Shared memory per warp of the dense numeric kernel (accumulator + bitmap).
+// Shared memory per warp of the dense numeric kernel (accumulator, bitmap,
+// table of the current batch's runs).
 template <class V, int W>
 constexpr size_t dense_warp_bytes() {
-    return (VOps<V>::has_val ? sizeof(V) * W : 0) + W / 8;
+    return (VOps<V>::has_val ? sizeof(V) * W : 0) + W / 8 + 32 * sizeof(DenseRun<V>);
 }
 
 template <class IT>
