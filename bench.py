@@ -337,8 +337,8 @@ def _checksum(torch, C):
 
 def train_sizer(sg, torch, inputs):
     """Predictor trained on the GPU on exact symbolic outputs of R-MAT scales
-    14-16 and ER matrices (the training recipe of the learned-sizing row)."""
-    pairs = [inputs.rmat(s, seed=500 + s) for s in (14, 15, 16)]
+    14-18 and ER matrices (the training recipe of the learned-sizing row)."""
+    pairs = [inputs.rmat(s, seed=500 + s) for s in (14, 15, 16, 17, 18)]
     pairs += [inputs.er_column_regular(1 << 15, d, 600 + d) for d in (8, 16)]
     dev = [(sg.to_device(A), sg.to_device(A)) for A in pairs]
     X, T = sg.sizer_training_set(dev)

@@ -217,16 +217,18 @@ typedef struct {
     int64_t total_flops;
 } spgemm_learned_result;
 
-/* spgemm_learned_multiply -- C = A.B with the symbolic phase of rows of at
- * most dense_min_flops products replaced by the predictor (params, plus
- * `margin` in log2 units of safety): those rows are multiplied straight into
- * predicted slots; rows that overflow are listed and multiplied again by the
- * exact two-phase path; dense rows keep their exact bitmap count.  Row
- * contents equal spgemm_symbolic + spgemm_numeric bit for bit.  With no
- * overflow, C is returned as slots (rowptr/rowend, gaps allowed); otherwise
- * as a plain compacted CSR.  All device memory comes from `alloc`; the call
- * waits for the stream (it reads sizes back three or four times).  Single
- * product; A may be a view (rowend). */
+/* spgemm_learned_multiply -- C = A.B with the symbolic phase replaced by
+ * the predictor (params, plus `margin` in log2 units of safety): every row is
+ * multiplied straight into a predicted slot (a dense row's column segments
+ * each fill a share of it in proportion to their chunks, then are packed
+ * together); rows that overflow are listed and multiplied again by the exact
+ * two-phase path.  Row contents equal spgemm_symbolic + spgemm_numeric bit
+ * for bit.  C is returned as slots (row i spans [rowptr[i], rowend[i]); gaps
+ * allowed; rowptr need not be monotone: re-run rows are placed in spare space
+ * after the slots) unless the re-run rows do not fit that space, in which
+ * case C is a plain compacted CSR (rowend NULL).  All device memory comes
+ * from `alloc`; the call waits for the stream (it reads sizes back three to
+ * five times).  Single product; A may be a view (rowend). */
 spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
                                       const spgemm_opts* opts, const float* params, float margin,
                                       void* stream, spgemm_alloc_fn alloc, void* ctx,

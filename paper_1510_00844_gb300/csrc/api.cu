@@ -77,6 +77,16 @@ int device_sm_count(int* smem_optin) {
 
 namespace sg {
 
+// Work units of the dense numeric kernel: each dense row of class t is cut
+// into dense_class_segments(t) segments.
+long long dense_unit_count(const Plan& P) {
+    long long u = 0;
+    for (int t = 0; t < kMaxDenseClasses; ++t)
+        u += (long long)P.class_count[kClassDense0 + t] * dense_class_segments(t);
+    return u;
+}
+
+
 static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void set_last_error(const char* msg) { g_last_error = msg; }

@@ -56,6 +56,16 @@ __device__ __forceinline__ T warp_sum(T x) {
 }
 
 template <class T>
+__device__ __forceinline__ T warp_min(T x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        T y = __shfl_xor_sync(kFull, x, d);
+        x = x < y ? x : y;
+    }
+    return x;
+}
+
+template <class T>
 __device__ __forceinline__ T warp_max(T x) {
 #pragma unroll
     for (int d = 16; d; d >>= 1) {

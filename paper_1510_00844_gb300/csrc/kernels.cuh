@@ -806,7 +806,9 @@ __global__ void __launch_bounds__(WARPS * 32)
                          const int32_t* __restrict__ runlen, DenseCursor* __restrict__ arena,
                          long long arena_stride, const int64_t* __restrict__ rpC, long long cap,
                          IT* __restrict__ ciC, V* __restrict__ vC, long long max_dense_n,
-                         unsigned long long* work, int* err) {
+                         unsigned long long* work, int* err, int64_t* __restrict__ rowend,
+                         int32_t* __restrict__ overflow, unsigned* overflow_count,
+                         int64_t* __restrict__ unit_cnt) {
     constexpr bool HV = VOps<V>::has_val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
@@ -858,21 +860,37 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int32_t* ccnt = chunkcnt + cx.chunk_base + cx.i * P;
         const int32_t* stab = segtab + cx.seg_base;
         const int32_t* rlen = runlen + cx.run_base;
-        // output offset: row start plus the entries of the chunks before cs
-        long long before = 0;
-        for (int c = lane; c < cs; c += 32) before += ccnt[c];
-        before = warp_sum(before);
-        long long out = rpC[r] + before;
-        long long seg_total = 0;
-        for (int c = cs + lane; c < ce; c += 32) seg_total += ccnt[c];
-        seg_total = warp_sum(seg_total);
-        if (seg_total == 0) continue;
-        const long long out_end = out + seg_total;
-        if (out_end > cap) {
-            if (lane == 0) atomicExch(err, (int)kDevCapacity);
-            continue;
+        // Slot mode (learned sizing, no symbolic pass): the row's predicted
+        // slot [rpC[r], rpC[r+1]) is split over its segments in proportion
+        // to their chunks; a segment that outgrows its share lists the row
+        // for an exact re-run.  Otherwise the chunk counts of the symbolic
+        // pass give the segment's exact place in C.
+        const bool slot_mode = rowend != nullptr;
+        long long out, out_end;
+        if (slot_mode) {
+            const long long span = rpC[r + 1] - rpC[r];
+            out = rpC[r] + span * cs / P;
+            out_end = rpC[r] + span * ce / P;
+        } else {
+            long long before = 0;
+            for (int c = lane; c < cs; c += 32) before += ccnt[c];
+            before = warp_sum(before);
+            out = rpC[r] + before;
+            long long seg_total = 0;
+            for (int c = cs + lane; c < ce; c += 32) seg_total += ccnt[c];
+            seg_total = warp_sum(seg_total);
+            if (seg_total == 0) continue;
+            out_end = out + seg_total;
+            if (out_end > cap) {
+                if (lane == 0) atomicExch(err, (int)kDevCapacity);
+                continue;
+            }
         }
-        // cursors at the segment start
+        const long long out_begin = out;
+        // cursors at the segment start; the smallest next column over all
+        // cursors names the next chunk with any product, so chunks without
+        // products are jumped over
+        int min_next = 0x7fffffff;
         for (long long p = a0 + lane; p < a1; p += 32) {
             long long k = (long long)ciA[p];
             long long s0 = rpB[k];
@@ -883,18 +901,21 @@ __global__ void __launch_bounds__(WARPS * 32)
             nc.left = (int)(s1 - c0p);
             nc.next_col = nc.left > 0 ? (int)ciB[c0p] : 0x7fffffff;
             cursor[p - a0] = nc;
+            min_next = min(min_next, nc.next_col);
         }
+        min_next = warp_min(min_next);
         __syncwarp();
-        for (int c = cs; c < ce; ++c) {
-            if (ccnt[c] == 0) continue;
+        for (int c = max(cs, min_next / W); c < ce;) {
             const long long c0 = (long long)c * W;
             const long long c1 = min(c0 + (long long)W, n);
+            int cnext = 0x7fffffff;  // smallest next column after this chunk
             for (long long bb = a0; bb < a1; bb += 32) {
                 const int nb = (int)min(32LL, a1 - bb);
                 const long long p = bb + lane;
                 DenseCursor cs2{0, 0, 0x7fffffff};
                 if (lane < nb) cs2 = cursor[p - a0];
                 const bool here = lane < nb && (long long)cs2.next_col < c1;
+                if (!here) cnext = min(cnext, cs2.next_col);
                 const unsigned hmask = __ballot_sync(kFull, here);
                 if (hmask == 0u) continue;
                 // the part of B(k,:) inside this chunk: runlen entries from the cursor
@@ -972,6 +993,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                     nc.left = cs2.left - len;
                     nc.next_col = nc.left > 0 ? (int)ciB[nc.pos] : 0x7fffffff;
                     cursor[p - a0] = nc;
+                    cnext = min(cnext, nc.next_col);
                 }
                 __syncwarp();
             }
@@ -1000,8 +1022,81 @@ __global__ void __launch_bounds__(WARPS * 32)
                 out += __shfl_sync(kFull, pincl, 31);
             }
             __syncwarp();
+            const int jump = warp_min(cnext) / W;
+            c = max(c + 1, jump);
         }
-        if (lane == 0 && out != out_end) atomicExch(err, (int)kDevCountMismatch);
+        if (lane == 0) {
+            if (!slot_mode) {
+                if (out != out_end) atomicExch(err, (int)kDevCountMismatch);
+            } else if (out > out_end) {
+                if (atomicCAS((unsigned long long*)&rowend[r], 0ull, ~0ull) == 0ull)
+                    overflow[atomicAdd(overflow_count, 1u)] = (int32_t)r;
+            } else {
+                unit_cnt[u] = out - out_begin;
+            }
+        }
+    }
+}
+
+// Learned sizing: close the gaps a slot-mode dense row leaves between its
+// segments (each segment moves left to follow the previous one) and set
+// rowend.  One warp per dense row; rows listed for a re-run are skipped.
+template <class IT, class V>
+__global__ void dense_slot_pack_kernel(const ProdDesc* __restrict__ D,
+                                       const long long* __restrict__ rb, int nprod,
+                                       const int32_t* __restrict__ rows,
+                                       const DevCounters* __restrict__ cnt,
+                                       const int64_t* __restrict__ rpC,
+                                       const int64_t* __restrict__ unit_cnt,
+                                       int64_t* __restrict__ rowend, IT* __restrict__ ciC,
+                                       V* __restrict__ vC) {
+    constexpr bool HV = VOps<V>::has_val;
+    const int lane = lane_id();
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long d0 = (long long)cnt->class_off[kClassDense0];
+    const long long nd = (long long)cnt->class_off[kNumClasses] - d0;
+    const unsigned long long* ub = cnt->unit_begin;
+    for (long long rr = warp; rr < nd; rr += nwarps) {
+        int b = 0;
+        while (b + 1 < kMaxDenseClasses &&
+               (long long)cnt->class_off[kClassDense0 + b + 1] - d0 <= rr)
+            ++b;
+        const int G = dense_class_segments(b);
+        const long long local = rr - ((long long)cnt->class_off[kClassDense0 + b] - d0);
+        const long long u0 = (long long)ub[b] + local * G;
+        const long long r = rows[d0 + rr];
+        if (rowend[r] != 0) continue;  // listed for a re-run
+        const int P = D[nprod > 1 ? find_prod(rb, nprod, r) : 0].P;
+        const long long start = rpC[r];
+        const long long span = rpC[r + 1] - start;
+        long long dst = start;
+        for (int g = 0; g < G; ++g) {
+            const int g0 = g * (kSegGrid / G);
+            const long long src = start + span * seg_chunk(g0, P) / P;
+            const long long len = unit_cnt[u0 + g];
+            if (src != dst) {
+                // dst < src: a forward copy in steps of 32 never overwrites
+                // an entry before it is read
+                for (long long q = 0; q < len; q += 32) {
+                    IT cv{};
+                    V vv{};
+                    const bool ok = q + lane < len;
+                    if (ok) {
+                        cv = ciC[src + q + lane];
+                        if constexpr (HV) vv = vC[src + q + lane];
+                    }
+                    __syncwarp();
+                    if (ok) {
+                        ciC[dst + q + lane] = cv;
+                        if constexpr (HV) vC[dst + q + lane] = vv;
+                    }
+                    __syncwarp();
+                }
+            }
+            dst += len;
+        }
+        if (lane == 0) rowend[r] = dst;
     }
 }
 

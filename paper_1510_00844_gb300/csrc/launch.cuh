@@ -106,15 +106,12 @@ cudaError_t sym_hash_bin(Plan& P, int bin, int64_t* rowcnt) {
     return cudaGetLastError();
 }
 
+// Tables of B the dense numeric kernel walks with: segment starts per B row
+// and the run length of every B entry inside its chunk.
 template <class IT>
-cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
+cudaError_t launch_dense_tables(Plan& P, unsigned char* ws) {
     WsLayout L = workspace_layout(P);
-    cudaError_t e = launch_zero_rows(P, rowcnt);
-    if (e != cudaSuccess) return e;
-    if ((e = sym_hash_bin<IT, 6, 8>(P, 0, rowcnt)) != cudaSuccess) return e;
-    if ((e = sym_hash_bin<IT, 8, 8>(P, 1, rowcnt)) != cudaSuccess) return e;
-    if ((e = sym_hash_bin<IT, 10, 8>(P, 2, rowcnt)) != cudaSuccess) return e;
-    if ((e = sym_hash_bin<IT, 11, 8>(P, 3, rowcnt)) != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const bool dense = P.device_sized || P.ndense > 0;
     if (dense && P.LB > 0) {
         long long total = P.LB * (kSegGrid + 1);
@@ -129,6 +126,20 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
                                                               (int32_t*)(ws + L.runlen), P.cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    return e;
+}
+
+template <class IT>
+cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
+    WsLayout L = workspace_layout(P);
+    cudaError_t e = launch_zero_rows(P, rowcnt);
+    if (e != cudaSuccess) return e;
+    if ((e = sym_hash_bin<IT, 6, 8>(P, 0, rowcnt)) != cudaSuccess) return e;
+    if ((e = sym_hash_bin<IT, 8, 8>(P, 1, rowcnt)) != cudaSuccess) return e;
+    if ((e = sym_hash_bin<IT, 10, 8>(P, 2, rowcnt)) != cudaSuccess) return e;
+    if ((e = sym_hash_bin<IT, 11, 8>(P, 3, rowcnt)) != cudaSuccess) return e;
+    const bool dense = P.device_sized || P.ndense > 0;
+    if ((e = launch_dense_tables<IT>(P, ws)) != cudaSuccess) return e;
     if (dense) {
         auto k = symbolic_dense_kernel<IT>;
         const int threads = 512;
@@ -174,7 +185,8 @@ cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT
 
 template <class IT, class V, int W, int WARPS>
 cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC, long long cap,
-                                 IT* colC, V* valC) {
+                                 IT* colC, V* valC, int64_t* rowend, int32_t* overflow,
+                                 unsigned* overflow_count) {
     WsLayout L = workspace_layout(P);
     auto k = numeric_dense_kernel<IT, V, W, WARPS>;
     size_t smem = (size_t)WARPS * dense_warp_bytes<V, W>();
@@ -188,7 +200,7 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
         P.d_descs, P.rb, P.nprod, P.rows, P.cnt, (const int32_t*)(ws + L.chunkcnt),
         (const int32_t*)(ws + L.segtab), (const int32_t*)(ws + L.runlen),
         (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, P.max_dense_n, work,
-        &P.cnt->err);
+        &P.cnt->err, rowend, overflow, overflow_count, P.unit_cnt);
     return cudaGetLastError();
 }
 
@@ -205,8 +217,10 @@ cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long 
     if ((e = num_hash_bin<IT, V, 11, 4>(P, 3, rpC, cap, colC, valC, rowend, overflow, overflow_count)) != cudaSuccess) return e;
     if (P.device_sized || P.ndense > 0) {
         e = P.W == kDenseW0
-                ? launch_numeric_dense<IT, V, kDenseW0, kDenseWarps0>(P, ws, rpC, cap, colC, valC)
-                : launch_numeric_dense<IT, V, kDenseW1, kDenseWarps1>(P, ws, rpC, cap, colC, valC);
+                ? launch_numeric_dense<IT, V, kDenseW0, kDenseWarps0>(P, ws, rpC, cap, colC, valC,
+                                                                      rowend, overflow, overflow_count)
+                : launch_numeric_dense<IT, V, kDenseW1, kDenseWarps1>(P, ws, rpC, cap, colC, valC,
+                                                                      rowend, overflow, overflow_count);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -232,8 +246,28 @@ cudaError_t prepare_numeric(Plan& P) {
                            : prepare_numeric_dense<IT, V, kDenseW1, kDenseWarps1>(P);
 }
 
+template <class IT, class V>
+cudaError_t launch_dense_slot_pack(Plan& P, const int64_t* rpC, void* colC, void* valC,
+                                   int64_t* rowend) {
+    if (P.ndense == 0) return cudaSuccess;
+    long long g = grid_for(P.ndense, 8, P.sm_count, 8);
+    count_launches(1);
+    dense_slot_pack_kernel<IT, V><<<(unsigned)g, 256, 0, P.stream>>>(
+        P.d_descs, P.rb, P.nprod, P.rows, P.cnt, rpC, P.unit_cnt, rowend, (IT*)colC, (V*)valC);
+    return cudaGetLastError();
+}
+
 #define SG_INSTANTIATE_IT(IT)                                                                   \
     template cudaError_t launch_analyze<IT>(Plan&);                                            \
+    template cudaError_t launch_dense_tables<IT>(Plan&, unsigned char*);                       \
+    template cudaError_t launch_dense_slot_pack<IT, double>(Plan&, const int64_t*, void*,      \
+                                                            void*, int64_t*);                  \
+    template cudaError_t launch_dense_slot_pack<IT, float>(Plan&, const int64_t*, void*,       \
+                                                           void*, int64_t*);                   \
+    template cudaError_t launch_dense_slot_pack<IT, int64_t>(Plan&, const int64_t*, void*,     \
+                                                             void*, int64_t*);                 \
+    template cudaError_t launch_dense_slot_pack<IT, NoVal>(Plan&, const int64_t*, void*,       \
+                                                           void*, int64_t*);                   \
     template cudaError_t launch_validate<IT>(const spgemm_csr&, int*, int, cudaStream_t);      \
     template cudaError_t launch_symbolic<IT>(Plan&, unsigned char*, int64_t*);                 \
     template cudaError_t launch_kslice_bounds<IT>(const spgemm_csr&, int, int64_t*, int,       \

@@ -3,14 +3,18 @@
 //
 //   1. plan with the predictor: every row gets a predicted capacity; rows of
 //      at most dense_min products are binned by that capacity;
-//   2. slots: capacities (exact counts for dense rows, from their bitmap
-//      symbolic pass) are scanned into slot offsets;
-//   3. numeric: every hash row is multiplied straight into its slot (same
-//      kernels, same ascending-k order as the two-phase path); a row that does
-//      not fit its slot or its table is listed instead of written;
+//   2. slots: the capacities are scanned into slot offsets (no symbolic pass
+//      for any row);
+//   3. numeric: every row is multiplied straight into its slot (same kernels,
+//      same ascending-k order as the two-phase path); a dense row's segments
+//      each take a share of the slot in proportion to their column chunks and
+//      are packed together afterwards; a row that does not fit its slot, its
+//      share or its hash table is listed instead of written;
 //   4. listed rows are multiplied again by the exact two-phase path, and C is
 //      assembled: with no listed row the slots already form C (row i spans
-//      [slot_i, rowend_i)); otherwise rows are compacted into a plain CSR.
+//      [slot_i, rowend_i)); listed rows whose exact output fits the spare
+//      space kept after the slots are written there (their slot start moves,
+//      C stays in slot form); otherwise rows are compacted into a plain CSR.
 // Row contents are identical to the two-phase result in every case.
 //
 // Device memory comes from a caller callback (spgemm_alloc_fn), since sizes
@@ -21,13 +25,12 @@
 
 namespace sg {
 
-// rowend of rows whose slot is exact (empty and dense rows).
+// rowend of the rows with no products.
 __global__ void fill_rowend_kernel(long long R, const unsigned char* __restrict__ cls,
                                    const int64_t* __restrict__ slots, int64_t* __restrict__ rowend) {
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R;
          r += (long long)gridDim.x * blockDim.x) {
-        const int c = cls[r];
-        if (c == kClassEmpty || c >= kClassDense0) rowend[r] = slots[r + 1];
+        if (cls[r] == kClassEmpty) rowend[r] = slots[r];
     }
 }
 
@@ -42,6 +45,18 @@ __global__ void gather_rows_kernel(long long cnt, const int32_t* __restrict__ li
         rp_sub[t] = rpA[r];
         re_sub[t] = reA ? reA[r] : rpA[r + 1];
         inv[r] = (int32_t)t;
+    }
+}
+
+// Listed rows re-run into the spare space at `base`: new slot start and end.
+__global__ void relocate_rows_kernel(long long cnt, const int32_t* __restrict__ list,
+                                     const int64_t* __restrict__ rp_x, long long base,
+                                     int64_t* __restrict__ slots, int64_t* __restrict__ rowend) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = list[t];
+        slots[r] = base + rp_x[t];
+        rowend[r] = base + rp_x[t + 1];
     }
 }
 
@@ -153,33 +168,32 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
     unsigned* ocount = (unsigned*)(ws + L.total);
     int32_t* olist = (int32_t*)(ws + L.total + al(sizeof(unsigned)));
     int32_t* inv = (int32_t*)(ws + L.total + al(sizeof(unsigned)) + al((size_t)m * 4));
-    // 2. slots: predicted capacities, exact counts for dense rows
+    // 2. slots: predicted capacities of all rows
     int64_t* slots = (int64_t*)get((size_t)(m + 1) * 8);
-    if (!slots) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
+    const long long units = sg::dense_unit_count(*P);
+    int64_t* unit_cnt = (int64_t*)get((size_t)std::max<long long>(units, 1) * 8);
+    if (!slots || !unit_cnt) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
+    P->unit_cnt = unit_cnt;
     cudaError_t e = cudaSuccess;
     if (m > 0) e = cudaMemcpyAsync(slots, P->cap, (size_t)m * 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(slots + m, 0, 8, s);
-    if (e == cudaSuccess && P->ndense > 0) {
-        // the dense symbolic pass (and the dense-path tables) only
-        unsigned long long saved[sg::kNumClasses];
-        for (int c = 0; c < sg::kNumClasses; ++c) saved[c] = P->class_count[c];
-        for (int b = 0; b < sg::kNumHashBins; ++b) P->class_count[sg::kClassHash0 + b] = 0;
-        P->class_count[sg::kClassEmpty] = 0;
-        e = P->it == SPGEMM_INDEX_I32 ? sg::launch_symbolic<int32_t>(*P, ws, slots)
-                                      : sg::launch_symbolic<int64_t>(*P, ws, slots);
-        for (int c = 0; c < sg::kNumClasses; ++c) P->class_count[c] = saved[c];
-    }
+    if (e == cudaSuccess && units > 0) e = cudaMemsetAsync(unit_cnt, 0, (size_t)units * 8, s);
+    if (e == cudaSuccess && P->ndense > 0)  // the tables the dense numeric kernel walks with
+        e = P->it == SPGEMM_INDEX_I32 ? sg::launch_dense_tables<int32_t>(*P, ws)
+                                      : sg::launch_dense_tables<int64_t>(*P, ws);
     if (e == cudaSuccess) e = sg::launch_exclusive_scan(slots, m + 1, (int64_t*)(ws + L.scan), s);
     long long total = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, slots + m, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return lcuda(e, "learned: slots");
-    // 3. numeric into the slots
+    // 3. numeric into the slots (with spare space after them for re-run rows)
+    const long long spare = total / 32 + 65536;
     int64_t* rowend = (int64_t*)get((size_t)std::max<long long>(m, 1) * 8);
-    unsigned char* col = get((size_t)total * isz);
-    unsigned char* val = vsz ? get((size_t)total * vsz) : nullptr;
+    unsigned char* col = get((size_t)(total + spare) * isz);
+    unsigned char* val = vsz ? get((size_t)(total + spare) * vsz) : nullptr;
     if (!rowend || !col || (vsz && !val)) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
     e = cudaMemsetAsync(ocount, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && m > 0) e = cudaMemsetAsync(rowend, 0, (size_t)m * 8, s);
     if (e == cudaSuccess) {
         const bool i32 = P->it == SPGEMM_INDEX_I32;
         switch (P->vt) {
@@ -198,6 +212,27 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
             default:
                 e = i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, ws, slots, total, col, nullptr, rowend, olist, ocount)
                         : sg::launch_numeric<int64_t, sg::NoVal>(*P, ws, slots, total, col, nullptr, rowend, olist, ocount);
+                break;
+        }
+    }
+    if (e == cudaSuccess && P->ndense > 0) {
+        const bool i32 = P->it == SPGEMM_INDEX_I32;
+        switch (P->vt) {
+            case SPGEMM_F64:
+                e = i32 ? sg::launch_dense_slot_pack<int32_t, double>(*P, slots, col, val, rowend)
+                        : sg::launch_dense_slot_pack<int64_t, double>(*P, slots, col, val, rowend);
+                break;
+            case SPGEMM_F32:
+                e = i32 ? sg::launch_dense_slot_pack<int32_t, float>(*P, slots, col, val, rowend)
+                        : sg::launch_dense_slot_pack<int64_t, float>(*P, slots, col, val, rowend);
+                break;
+            case SPGEMM_I64:
+                e = i32 ? sg::launch_dense_slot_pack<int32_t, int64_t>(*P, slots, col, val, rowend)
+                        : sg::launch_dense_slot_pack<int64_t, int64_t>(*P, slots, col, val, rowend);
+                break;
+            default:
+                e = i32 ? sg::launch_dense_slot_pack<int32_t, sg::NoVal>(*P, slots, col, nullptr, rowend)
+                        : sg::launch_dense_slot_pack<int64_t, sg::NoVal>(*P, slots, col, nullptr, rowend);
                 break;
         }
     }
@@ -262,6 +297,23 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
     if (!ws2 || !rp_x) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
     int64_t nnz_x = 0;
     if ((st = spgemm_symbolic(P2, ws2, ws2b, rp_x, &nnz_x)) != SPGEMM_OK) return st;
+    if (nnz_x <= spare) {  // re-run rows go to the spare space; C stays in slot form
+        unsigned char* col_sp = col + (size_t)total * isz;
+        unsigned char* val_sp = vsz ? val + (size_t)total * vsz : nullptr;
+        if ((st = spgemm_numeric(P2, ws2, ws2b, rp_x, col_sp, val_sp)) != SPGEMM_OK) return st;
+        sg::count_launches(1);
+        sg::relocate_rows_kernel<<<(nover + 255) / 256, 256, 0, s>>>(nover, olist, rp_x, total,
+                                                                      slots, rowend);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return lcuda(e, "learned: relocate");
+        out->rowptr = slots;
+        out->rowend = rowend;
+        out->col = col;
+        out->val = val;
+        out->nnz = total + nnz_x;
+        return SPGEMM_OK;
+    }
     unsigned char* col_x = get((size_t)nnz_x * isz);
     unsigned char* val_x = vsz ? get((size_t)nnz_x * vsz) : nullptr;
     if (!col_x || (vsz && !val_x)) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");

@@ -40,6 +40,7 @@ struct spgemm_plan_s {
     int64_t* cap = nullptr;          // predicted (learned plans) or flops bound per row
     const float* prm = nullptr;      // row-size predictor parameters (learned plans)
     float margin = 0.f;              // log2 safety margin added to the prediction
+    int64_t* unit_cnt = nullptr;     // slot-mode dense numeric: entries per work unit
     // host copies of the row analysis (host-synced plans)
     unsigned long long class_count[sg::kNumClasses] = {};
     long long class_off[sg::kNumClasses + 1] = {};
@@ -93,6 +94,12 @@ template <class IT>
 cudaError_t launch_validate(const spgemm_csr& M, int* err, int sm_count, cudaStream_t s);
 template <class IT>
 cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt);
+template <class IT>
+cudaError_t launch_dense_tables(Plan& P, unsigned char* ws);
+template <class IT, class V>
+cudaError_t launch_dense_slot_pack(Plan& P, const int64_t* rpC, void* colC, void* valC,
+                                   int64_t* rowend);
+long long dense_unit_count(const Plan& P);
 template <class IT, class V>
 cudaError_t prepare_numeric(Plan& P);
 template <class IT, class V>

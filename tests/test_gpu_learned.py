@@ -94,3 +94,55 @@ def test_learned_value_types(sg, trained, value):
         assert bool((Cc.val == P.val).all())
     R = oracle.spgemm(A, A, semiring="or_and" if value == "none" else "plus_times")
     assert_pattern_equal(Cc, R)
+
+
+@pytest.mark.parametrize("margin,value", [(40.0, "u01_f64"), (0.3, "u01_f64"), (-1.0, "u01_f64"),
+                                          (0.3, "u11_f32"), (0.3, "int"), (0.3, "none")])
+def test_learned_dense_rows_without_symbolic(sg, trained, margin, value):
+    """Rows above the dense threshold take predicted slots too: their column
+    segments (up to 8 per row at this scale) each fill a share of the slot and
+    are packed together; a segment that outgrows its share sends the row to
+    the exact re-run.  Rows equal the two-phase path bit for bit."""
+    A = inputs.rmat(14, seed=91, value=value)
+    dA = sg.to_device(A)
+    semiring = 1 if value == "none" else 0
+    p = sg.plan(dA, dA, semiring=semiring)
+    inf = p.info()
+    assert inf["rows_dense"] > 0 and inf["max_row_flops"] >= 1 << 18   # multi-segment rows
+    C, stats = sg.learned_multiply(dA, dA, trained, margin=margin, semiring=semiring)
+    P = sg.spgemm(dA, dA, semiring=semiring)
+    Cc = sg.compact(C)
+    assert bool((Cc.rowptr == P.rowptr).all()) and bool((Cc.col == P.col).all())
+    if value != "none":
+        assert bool((Cc.val == P.val).all())
+    if margin == 40.0:
+        assert stats["overflow_rows"] == 0 and stats["slots"]
+    if margin == -1.0:
+        assert stats["overflow_rows"] > 0
+
+
+def test_learned_rerun_rows_go_to_spare_space(sg, trained):
+    """With margin -40 every slot shrinks to its lower bound max_k |B(k,:)|:
+    rows of A with one entry fit exactly, the ten rows with three entries
+    overflow.  Their exact re-run output is small, so it lands in the spare
+    space after the slots and C stays in slot form (no compaction)."""
+    import numpy as np
+    n = 4096
+    perm = inputs.permutation(n, 5)
+    rng = np.random.default_rng(6)
+    rows = list(range(n))
+    cols = list(perm)
+    heavy = rng.choice(n, 10, replace=False)
+    for r in heavy:
+        for k in rng.choice(n, 2, replace=False):
+            rows.append(int(r))
+            cols.append(int(k))
+    A = inputs.coo_to_csr(n, n, rows, cols, rng.random(len(rows)), index_dtype=np.int32)
+    B = inputs.er_column_regular(n, 8, 7)
+    dA, dB = sg.to_device(A), sg.to_device(B)
+    C, stats = sg.learned_multiply(dA, dB, trained, margin=-40.0)
+    assert 1 <= stats["overflow_rows"] <= 10 and stats["slots"]
+    P = sg.spgemm(dA, dB)
+    Cc = sg.compact(C)
+    assert bool((Cc.rowptr == P.rowptr).all())
+    assert bool((Cc.col == P.col).all()) and bool((Cc.val == P.val).all())
