@@ -91,7 +91,13 @@ typedef struct {
                                 0 = 1024, else 32..1024 (autotuned knob) */
     int32_t max_row_nnz;     /* device-sized plans: bound on the entries of a dense row of A
                                 (cursor arena slot), 0 = 65536 */
-    int32_t reserved[3];     /* must be zero */
+    int32_t hash_shift;      /* hash-table sizing (autotuned knob): a hash row with f products
+                                goes to the smallest bin whose bound is >= f << hash_shift, so
+                                its table has at least 2^(1+hash_shift) f slots; 0..2 */
+    int32_t seg_log2;        /* dense work-unit size (autotuned knob): a dense row with about
+                                2^t products is cut into 2^clamp(t+1-seg_log2, 0, 4) column
+                                segments, one warp each; 0 = 16, else 10..22 */
+    int32_t reserved[1];     /* must be zero */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s* spgemm_plan_t;

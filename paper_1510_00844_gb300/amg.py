@@ -11,7 +11,7 @@ nnz(R^T A), so nnz(A_l) bounds both products of level l."""
 from __future__ import annotations
 
 import ctypes
-from typing import List
+from typing import List, Optional
 
 import torch
 
@@ -20,7 +20,7 @@ from . import spgemm as sg
 
 class GalerkinChain:
     def __init__(self, A0: sg.DeviceCSR, Rs: List[sg.DeviceCSR], stream: torch.cuda.Stream,
-                 max_row_nnz: int = 64):
+                 max_row_nnz: int = 64, tuning: Optional[sg.Tuning] = None):
         self.stream = stream
         self.Rs = Rs
         dev = A0.rowptr.device
@@ -44,8 +44,8 @@ class GalerkinChain:
             An = sg.DeviceCSR(n_c, n_c, torch.empty(n_c + 1, dtype=torch.int64, device=dev),
                               torch.empty(cap, dtype=idt, device=dev),
                               torch.empty(cap, dtype=vdt, device=dev))
-            p1 = sg.device_plan([Rt], [A], stream=stream, max_row_nnz=max_row_nnz)
-            p2 = sg.device_plan([T], [R], stream=stream, max_row_nnz=max_row_nnz)
+            p1 = sg.device_plan([Rt], [A], stream=stream, max_row_nnz=max_row_nnz, tuning=tuning)
+            p2 = sg.device_plan([T], [R], stream=stream, max_row_nnz=max_row_nnz, tuning=tuning)
             self.levels.append(dict(R=R, cR=cR, tws=tws, Rt=Rt, T=T, A=An, p1=p1, p2=p2, cap=cap))
             A = An
         self.graph = None

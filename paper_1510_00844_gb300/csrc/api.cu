@@ -82,7 +82,7 @@ namespace sg {
 long long dense_unit_count(const Plan& P) {
     long long u = 0;
     for (int t = 0; t < kMaxDenseClasses; ++t)
-        u += (long long)P.class_count[kClassDense0 + t] * dense_class_segments(t);
+        u += (long long)P.class_count[kClassDense0 + t] * dense_class_segments(t, P.seg_log2);
     return u;
 }
 
@@ -144,6 +144,10 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     if (o.dense_min_flops != 0 && (o.dense_min_flops < 32 || o.dense_min_flops > 1024))
         return fail(SPGEMM_ERR_INVALID_ARG, "dense_min_flops must be 0 or in [32, 1024]");
     if (o.max_row_nnz < 0) return fail(SPGEMM_ERR_INVALID_ARG, "max_row_nnz must be >= 0");
+    if (o.hash_shift < 0 || o.hash_shift > 2)
+        return fail(SPGEMM_ERR_INVALID_ARG, "hash_shift must be in [0, 2]");
+    if (o.seg_log2 != 0 && (o.seg_log2 < 10 || o.seg_log2 > 22))
+        return fail(SPGEMM_ERR_INVALID_ARG, "seg_log2 must be 0 or in [10, 22]");
     if (!A || !B) return fail(SPGEMM_ERR_INVALID_ARG, "A or B is NULL");
     const int vt = kernel_value_type(&A[0], &o);
     const bool need_vals = vt != SPGEMM_BOOL;
@@ -190,6 +194,8 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->prm = sizer_params;
     P->margin = sizer_margin;
     P->dense_min = o.dense_min_flops ? o.dense_min_flops : 1024;
+    P->hash_shift = o.hash_shift;
+    P->seg_log2 = o.seg_log2 ? o.seg_log2 : 16;
     P->sm_count = device_sm_count(&P->smem_optin);
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
     P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;

@@ -6,7 +6,8 @@ namespace sg {
 
 // Class offsets (exclusive scan of the counts) and the dense work-unit
 // prefix, one thread.
-__global__ void class_offsets_kernel(DevCounters* cnt) {
+__global__ void class_offsets_kernel(DevCounters* cnt, int seg_log2) {
+    cnt->seg_log2 = seg_log2;
     unsigned long long s = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         cnt->class_cursor[c] = s;
@@ -17,7 +18,8 @@ __global__ void class_offsets_kernel(DevCounters* cnt) {
     unsigned long long u = 0;
     for (int t = 0; t < kMaxDenseClasses; ++t) {
         cnt->unit_begin[t] = u;
-        u += cnt->class_count[kClassDense0 + t] * (unsigned long long)dense_class_segments(t);
+        u += cnt->class_count[kClassDense0 + t] *
+             (unsigned long long)dense_class_segments(t, seg_log2);
     }
     cnt->unit_begin[kMaxDenseClasses] = u;
 }
@@ -153,7 +155,7 @@ __global__ void product_rowptr_kernel(long long R, const long long* __restrict__
 cudaError_t launch_binning(Plan& P) {
     const long long R = P.R;
     count_launches(1);
-    class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt);
+    class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt, P.seg_log2);
     if (R > 0) {
         int blocks = (int)std::max<long long>(1, std::min<long long>((R + 1023) / 1024, (long long)P.sm_count * 4));
         count_launches(1);

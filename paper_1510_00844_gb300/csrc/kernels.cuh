@@ -70,7 +70,8 @@ struct DevCounters {
     unsigned long long max_dense_len;    // longest A row among dense rows
     int err;
     int unsupported;
-    int pad[30];
+    int seg_log2;                        // dense work-unit size of the plan
+    int pad[29];
 };
 
 // Product owning global row r: the largest p with rb[p] <= r.
@@ -126,14 +127,17 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Class of a row with `flops` products: EMPTY, the smallest hash bin that
-// holds it while flops <= dense_min (<= 1024), else the dense bucket of
-// floor(log2 flops), largest first.
-__host__ __device__ __forceinline__ int row_class(long long flops, int dense_min) {
+// holds flops << hash_shift while flops <= dense_min (<= 1024; the largest
+// bin takes the rest), else the dense bucket of floor(log2 flops), largest
+// first.
+__host__ __device__ __forceinline__ int row_class(long long flops, int dense_min,
+                                                  int hash_shift = 0) {
     if (flops == 0) return kClassEmpty;
     if (flops <= dense_min) {
 #pragma unroll
-        for (int b = 0; b < kNumHashBins; ++b)
-            if (flops <= hash_bin_flops(b)) return kClassHash0 + b;
+        for (int b = 0; b < kNumHashBins - 1; ++b)
+            if ((flops << hash_shift) <= hash_bin_flops(b)) return kClassHash0 + b;
+        return kClassHash0 + kNumHashBins - 1;
     }
 #ifdef __CUDA_ARCH__
     int lg = 63 - __clzll(flops);
@@ -147,9 +151,9 @@ __host__ __device__ __forceinline__ int row_class(long long flops, int dense_min
 
 // Segments per row of dense class t (floor(log2 flops) = kDenseMaxLog2 - t):
 // about 2^16 products per segment, at most kSegGrid.
-__host__ __device__ __forceinline__ int dense_class_segments(int t) {
+__host__ __device__ __forceinline__ int dense_class_segments(int t, int seg_log2) {
     const int lg = kDenseMaxLog2 - t;
-    int sh = lg + 1 - 16;
+    int sh = lg + 1 - seg_log2;
     if (sh < 0) sh = 0;
     if (sh > 4) sh = 4;  // kSegGrid = 16
     return 1 << sh;
@@ -176,7 +180,7 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
                                int dense_min, int64_t* __restrict__ flops_out,
                                unsigned char* __restrict__ cls_out, DevCounters* cnt,
                                const float* __restrict__ prm, float margin,
-                               int64_t* __restrict__ cap_out) {
+                               int64_t* __restrict__ cap_out, int hash_shift) {
     __shared__ unsigned long long hist[kNumClasses];
     __shared__ unsigned long long blk_total, blk_max, blk_dlen;
     __shared__ int blk_unsup;
@@ -239,8 +243,9 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
         if (lane == 0) {
             flops_out[r] = f;
             if (cap_out) cap_out[r] = prm ? cap : f;
-            int cl = row_class(f, dense_min);
-            if (prm && cl > kClassEmpty && cl < kClassDense0) cl = row_class(cap > 0 ? cap : 1, dense_min);
+            int cl = row_class(f, dense_min, hash_shift);
+            if (prm && cl > kClassEmpty && cl < kClassDense0)
+                cl = row_class(cap > 0 ? cap : 1, dense_min, hash_shift);
             cls_out[r] = (unsigned char)cl;
             if (cl >= kClassDense0) {
                 if (c.n > max_dense_n) blk_unsup = 1;
@@ -833,7 +838,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (u >= total_units) break;
         int b = 0;
         while (b + 1 < kMaxDenseClasses && (long long)ub[b + 1] <= u) ++b;
-        const int G = dense_class_segments(b);
+        const int G = dense_class_segments(b, cnt->seg_log2);
         const long long local = u - (long long)ub[b];
         const long long rr = (long long)(cnt->class_off[kClassDense0 + b] -
                                          cnt->class_off[kClassDense0]) + local / G;
@@ -1062,7 +1067,7 @@ __global__ void dense_slot_pack_kernel(const ProdDesc* __restrict__ D,
         while (b + 1 < kMaxDenseClasses &&
                (long long)cnt->class_off[kClassDense0 + b + 1] - d0 <= rr)
             ++b;
-        const int G = dense_class_segments(b);
+        const int G = dense_class_segments(b, cnt->seg_log2);
         const long long local = rr - ((long long)cnt->class_off[kClassDense0 + b] - d0);
         const long long u0 = (long long)ub[b] + local * G;
         const long long r = rows[d0 + rr];

@@ -51,7 +51,7 @@ cudaError_t launch_analyze(Plan& P) {
     count_launches(1);
     k<<<(unsigned)g, 256, 0, P.stream>>>(P.R, P.d_descs, P.rb, P.nprod, P.max_dense_n,
                                            P.dense_min, P.flops, P.cls, P.cnt, P.prm, P.margin,
-                                           P.cap);
+                                           P.cap, P.hash_shift);
     return cudaGetLastError();
 }
 
@@ -93,7 +93,8 @@ cudaError_t sym_hash_bin(Plan& P, int bin, int64_t* rowcnt) {
     const int c = kClassHash0 + bin;
     const long long nrows = (long long)P.class_count[c];
     if (!P.device_sized && nrows == 0) return cudaSuccess;
-    if (P.device_sized && bin > 0 && hash_bin_flops(bin - 1) >= P.dense_min) return cudaSuccess;
+    if (P.device_sized && bin > 0 && (hash_bin_flops(bin - 1) >> P.hash_shift) >= P.dense_min)
+        return cudaSuccess;
     auto k = symbolic_hash_kernel<IT, LOG2T, WARPS>;
     size_t smem = (size_t)WARPS * (1u << LOG2T) * sizeof(K);
     cudaError_t e = allow_smem(k, smem);
@@ -168,7 +169,8 @@ cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT
     const int c = kClassHash0 + bin;
     const long long nrows = (long long)P.class_count[c];
     if (!P.device_sized && nrows == 0) return cudaSuccess;
-    if (P.device_sized && bin > 0 && hash_bin_flops(bin - 1) >= P.dense_min) return cudaSuccess;
+    if (P.device_sized && bin > 0 && (hash_bin_flops(bin - 1) >> P.hash_shift) >= P.dense_min)
+        return cudaSuccess;
     auto k = numeric_hash_kernel<IT, V, LOG2T, WARPS>;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
     size_t smem = (size_t)WARPS * ((1u << LOG2T) * (sizeof(K) + vb) + 256 * sizeof(int));

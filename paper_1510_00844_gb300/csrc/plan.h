@@ -26,6 +26,8 @@ struct spgemm_plan_s {
     long long max_n = 0;     // largest n of the batch
     long long max_dense_n = 0;
     int dense_min = 1024;    // rows with more products than this are dense
+    int hash_shift = 0;      // hash rows are binned by flops << hash_shift
+    int seg_log2 = 16;       // dense work units of about 2^seg_log2 products
     bool device_sized = false;  // no host readback: sizes are upper bounds
     // plan workspace
     unsigned char* pws = nullptr;

@@ -11,6 +11,7 @@ Names follow the C entry points: ``plan``, ``symbolic``, ``numeric``,
 from __future__ import annotations
 
 import ctypes
+from dataclasses import dataclass
 import dataclasses
 import os
 from typing import List, Optional, Sequence
@@ -44,7 +45,27 @@ class _Csr(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("semiring", ctypes.c_int32), ("checked", ctypes.c_int32),
                 ("dense_chunk", ctypes.c_int32), ("dense_min_flops", ctypes.c_int32),
-                ("max_row_nnz", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("max_row_nnz", ctypes.c_int32), ("hash_shift", ctypes.c_int32),
+                ("seg_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+
+
+@dataclass(frozen=True)
+class Tuning:
+    """Runtime knobs of a plan (spgemm_opts): dense-row chunk width (0, 1024
+    or 2048), dense threshold in products (0 = 1024, else 32..1024), hash
+    table sizing shift (0..2) and dense work-unit size log2 (0 = 16, else
+    10..22).  The autotuner (autotune.py) searches them."""
+    dense_chunk: int = 0
+    dense_min_flops: int = 0
+    hash_shift: int = 0
+    seg_log2: int = 0
+
+
+def _make_opts(semiring: int, checked: bool = False, tuning: Optional[Tuning] = None,
+               dense_chunk: int = 0, dense_min_flops: int = 0, max_row_nnz: int = 0) -> "_Opts":
+    t = tuning or Tuning()
+    return _Opts(semiring, 1 if checked else 0, t.dense_chunk or dense_chunk,
+                 t.dense_min_flops or dense_min_flops, max_row_nnz, t.hash_shift, t.seg_log2)
 
 
 class _Info(ctypes.Structure):
@@ -192,11 +213,12 @@ class Plan:
     workspaces alive until closed."""
 
     def __init__(self, A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES,
-                 checked: bool = False, stream=None, dense_chunk: int = 0):
+                 checked: bool = False, stream=None, dense_chunk: int = 0,
+                 tuning: Optional[Tuning] = None):
         self.A, self.B = A, B
         self.device = A.rowptr.device
         self._cA, self._cB = _csr(A), _csr(B)
-        self._opts = _Opts(semiring, 1 if checked else 0, dense_chunk)
+        self._opts = _make_opts(semiring, checked, tuning, dense_chunk)
         self.pattern_only = semiring == OR_AND or A.val is None
         self.stream = stream
         self._plan_ws = _workspace(_lib.spgemm_plan_workspace_size(A.nrows), self.device)
@@ -228,8 +250,8 @@ class Plan:
 
 
 def plan(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool = False,
-         stream=None, dense_chunk: int = 0) -> Plan:
-    return Plan(A, B, semiring, checked, stream, dense_chunk)
+         stream=None, dense_chunk: int = 0, tuning: Optional[Tuning] = None) -> Plan:
+    return Plan(A, B, semiring, checked, stream, dense_chunk, tuning)
 
 
 class BatchPlan(Plan):
@@ -238,14 +260,16 @@ class BatchPlan(Plan):
 
     def __init__(self, As: Sequence[DeviceCSR], Bs: Sequence[DeviceCSR], semiring: int = PLUS_TIMES,
                  checked: bool = False, stream=None, dense_chunk: int = 0,
-                 dense_min_flops: int = 0, device_sized: bool = False, max_row_nnz: int = 0):
+                 dense_min_flops: int = 0, device_sized: bool = False, max_row_nnz: int = 0,
+                 tuning: Optional[Tuning] = None):
         self.As, self.Bs = list(As), list(Bs)
         self.A, self.B = self.As[0], self.Bs[0]
         self.device = self.A.rowptr.device
         self.count = len(self.As)
         self._cAs = (_Csr * self.count)(*[_csr(M) for M in self.As])
         self._cBs = (_Csr * self.count)(*[_csr(M) for M in self.Bs])
-        self._opts = _Opts(semiring, 1 if checked else 0, dense_chunk, dense_min_flops, max_row_nnz)
+        self._opts = _make_opts(semiring, checked, tuning, dense_chunk, dense_min_flops,
+                                max_row_nnz)
         self.pattern_only = semiring == OR_AND or self.A.val is None
         self.stream = stream
         self.device_sized = device_sized
@@ -266,14 +290,17 @@ class BatchPlan(Plan):
 
 
 def batch_plan(As, Bs, semiring: int = PLUS_TIMES, checked: bool = False, stream=None,
-               dense_chunk: int = 0, dense_min_flops: int = 0) -> BatchPlan:
-    return BatchPlan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops)
+               dense_chunk: int = 0, dense_min_flops: int = 0,
+               tuning: Optional[Tuning] = None) -> BatchPlan:
+    return BatchPlan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops,
+                     tuning=tuning)
 
 
 def device_plan(As, Bs, semiring: int = PLUS_TIMES, stream=None, dense_chunk: int = 0,
-                dense_min_flops: int = 0, max_row_nnz: int = 0) -> BatchPlan:
+                dense_min_flops: int = 0, max_row_nnz: int = 0,
+                tuning: Optional[Tuning] = None) -> BatchPlan:
     return BatchPlan(As, Bs, semiring, False, stream, dense_chunk, dense_min_flops,
-                     device_sized=True, max_row_nnz=max_row_nnz)
+                     device_sized=True, max_row_nnz=max_row_nnz, tuning=tuning)
 
 
 def execute(p: BatchPlan, rowptrC: torch.Tensor, capacity: int, colC: torch.Tensor,
@@ -311,9 +338,9 @@ def split_batch(p: BatchPlan, rowptrC: torch.Tensor, colC: torch.Tensor,
 
 def batch_spgemm(As, Bs, semiring: int = PLUS_TIMES, checked: bool = False, stream=None,
                  verify: bool = False, dense_chunk: int = 0,
-                 dense_min_flops: int = 0) -> List[DeviceCSR]:
+                 dense_min_flops: int = 0, tuning: Optional[Tuning] = None) -> List[DeviceCSR]:
     """All products C_p = As[p] . Bs[p] with one plan (one launch per phase)."""
-    p = batch_plan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops)
+    p = batch_plan(As, Bs, semiring, checked, stream, dense_chunk, dense_min_flops, tuning)
     rowptrC, nnz = symbolic(p)
     colC, valC = alloc_output(p, nnz)
     numeric(p, rowptrC, colC, valC)
@@ -354,9 +381,10 @@ def alloc_output(p: Plan, nnz: int):
 
 
 def spgemm(A: DeviceCSR, B: DeviceCSR, semiring: int = PLUS_TIMES, checked: bool = False,
-           stream=None, verify: bool = False, dense_chunk: int = 0) -> DeviceCSR:
+           stream=None, verify: bool = False, dense_chunk: int = 0,
+           tuning: Optional[Tuning] = None) -> DeviceCSR:
     """C = A.B: plan, symbolic, allocate C, numeric."""
-    p = plan(A, B, semiring, checked, stream, dense_chunk)
+    p = plan(A, B, semiring, checked, stream, dense_chunk, tuning)
     rowptrC, nnz = symbolic(p)
     colC, valC = alloc_output(p, nnz)
     numeric(p, rowptrC, colC, valC)
@@ -517,7 +545,8 @@ def sizer_training_set(pairs, stream=None):
 
 
 def learned_multiply(A: DeviceCSR, B: DeviceCSR, params: torch.Tensor, margin: float = 0.25,
-                     semiring: int = PLUS_TIMES, stream=None, dense_min_flops: int = 0):
+                     semiring: int = PLUS_TIMES, stream=None, dense_min_flops: int = 0,
+                     tuning: Optional[Tuning] = None):
     """C = A.B with learned sizing (spgemm_learned_multiply).  Returns
     (C, stats); C carries rowend when it is returned as slots."""
     keep = []
@@ -530,7 +559,7 @@ def learned_multiply(A: DeviceCSR, B: DeviceCSR, params: torch.Tensor, margin: f
 
     cb = _ALLOC_FN(alloc)
     cA, cB = _csr(A), _csr(B)
-    opts = _Opts(semiring, 0, 0, dense_min_flops, 0)
+    opts = _make_opts(semiring, False, tuning, 0, dense_min_flops)
     res = _LearnedResult()
     _check(_lib.spgemm_learned_multiply(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(opts),
                                         ctypes.c_void_p(params.data_ptr()), ctypes.c_float(margin),
