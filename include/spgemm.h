@@ -96,7 +96,9 @@ typedef struct {
                                 its table has at least 2^(1+hash_shift) f slots; 0..2 */
     int32_t seg_log2;        /* dense work-unit size (autotuned knob): a dense row with about
                                 2^t products is cut into 2^clamp(t+1-seg_log2, 0, 4) column
-                                segments, one warp each; 0 = 16, else 10..22 */
+                                segments, one warp each; 0 = chosen per plan from
+                                the flops and the resident warps (16 for device-sized
+                                plans), else 10..22 */
     int32_t reserved[1];     /* must be zero */
 } spgemm_opts;
 

@@ -23,8 +23,14 @@ SPACE: Dict[str, Tuple[int, ...]] = {
     "dense_min_flops": (1024, 512, 256),
     "hash_shift": (0, 1),
     "dense_chunk": (1024, 2048),
-    "seg_log2": (16, 14, 18, 20),
+    "seg_log2": (16, 18, 20, 22),
 }
+
+
+def _normal(t: Tuning) -> Tuning:
+    """Spells out the library defaults (0 = default) so that equal settings
+    are measured once."""
+    return dataclasses.replace(t, dense_min_flops=t.dense_min_flops or 1024)
 
 
 def descend(measure: Callable[[Tuning], float], space: Dict[str, Iterable[int]] = SPACE,
@@ -33,11 +39,14 @@ def descend(measure: Callable[[Tuning], float], space: Dict[str, Iterable[int]] 
     measured time beats the best so far by more than min_gain (relative).
     Returns (best tuning, {tuning: time}) with every measured candidate."""
     table: Dict[Tuning, float] = {}
+    seen: Dict[Tuning, float] = {}
 
     def cost(t: Tuning) -> float:
-        if t not in table:
-            table[t] = float(measure(t))
-        return table[t]
+        key = _normal(t)
+        if key not in seen:
+            seen[key] = float(measure(t))
+        table[t] = seen[key]
+        return seen[key]
 
     best = base
     best_ms = cost(best)

@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/spgemm.h): argument checks,
 // plan bookkeeping, dispatch on index/value type, error reporting.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -195,7 +196,7 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->margin = sizer_margin;
     P->dense_min = o.dense_min_flops ? o.dense_min_flops : 1024;
     P->hash_shift = o.hash_shift;
-    P->seg_log2 = o.seg_log2 ? o.seg_log2 : 16;
+    P->seg_log2 = o.seg_log2 ? o.seg_log2 : 16;  // host-synced plans refine it below
     P->sm_count = device_sm_count(&P->smem_optin);
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
     P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;
@@ -347,6 +348,17 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     P->max_dense_len = (long long)h.max_dense_len;
     e = prepare();
     if (e != cudaSuccess) return bail(cuda_fail(e, "plan: numeric setup"));
+    if (!o.seg_log2 && P->ndense > 0) {
+        // dense work units of about total_flops / (4 x resident dense warps)
+        // products: few, long units on big products, enough of them on small
+        const double warps = (double)std::max<long long>(1, P->dense_grid * P->dense_warps_per_block);
+        const double per = (double)std::max<long long>(1, P->total_flops) / (4.0 * warps);
+        P->seg_log2 = std::min(20, std::max(14, (int)std::floor(std::log2(per))));
+        if (P->seg_log2 != 16) {
+            e = sg::launch_class_offsets(*P);
+            if (e != cudaSuccess) return bail(cuda_fail(e, "plan: work units"));
+        }
+    }
     *plan_out = P;
     return SPGEMM_OK;
 }

@@ -152,6 +152,12 @@ __global__ void product_rowptr_kernel(long long R, const long long* __restrict__
     }
 }
 
+cudaError_t launch_class_offsets(Plan& P) {
+    count_launches(1);
+    class_offsets_kernel<<<1, 1, 0, P.stream>>>(P.cnt, P.seg_log2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_binning(Plan& P) {
     const long long R = P.R;
     count_launches(1);

@@ -150,7 +150,9 @@ __host__ __device__ __forceinline__ int row_class(long long flops, int dense_min
 }
 
 // Segments per row of dense class t (floor(log2 flops) = kDenseMaxLog2 - t):
-// about 2^16 products per segment, at most kSegGrid.
+// about 2^seg_log2 products per segment (a plan knob; by default chosen from
+// the plan's flops so that big products get fewer, longer units), at most
+// kSegGrid.
 __host__ __device__ __forceinline__ int dense_class_segments(int t, int seg_log2) {
     const int lg = kDenseMaxLog2 - t;
     int sh = lg + 1 - seg_log2;

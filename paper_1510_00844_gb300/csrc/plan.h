@@ -84,6 +84,7 @@ cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long 
 size_t scan_temp_bytes(long long N);
 cudaError_t launch_exclusive_scan(int64_t* x, long long N, int64_t* temp, cudaStream_t s);
 cudaError_t launch_binning(Plan& P);
+cudaError_t launch_class_offsets(Plan& P);
 cudaError_t launch_zero_rows(const Plan& P, int64_t* rowcnt);
 cudaError_t launch_product_rowptr(const Plan& P, const int64_t* g, int64_t* out);
 

@@ -53,7 +53,7 @@ class _Opts(ctypes.Structure):
 class Tuning:
     """Runtime knobs of a plan (spgemm_opts): dense-row chunk width (0, 1024
     or 2048), dense threshold in products (0 = 1024, else 32..1024), hash
-    table sizing shift (0..2) and dense work-unit size log2 (0 = 16, else
+    table sizing shift (0..2) and dense work-unit size log2 (0 = per plan, else
     10..22).  The autotuner (autotune.py) searches them."""
     dense_chunk: int = 0
     dense_min_flops: int = 0

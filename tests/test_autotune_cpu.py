@@ -7,7 +7,7 @@ from paper_1510_00844_gb300.spgemm import Tuning
 
 
 def test_descent_finds_the_minimum_of_a_separable_cost():
-    best_vals = {"dense_min_flops": 256, "hash_shift": 1, "dense_chunk": 2048, "seg_log2": 14}
+    best_vals = {"dense_min_flops": 256, "hash_shift": 1, "dense_chunk": 2048, "seg_log2": 18}
 
     def cost(t: Tuning) -> float:
         c = 10.0
@@ -26,6 +26,14 @@ def test_descent_keeps_the_default_without_a_real_gain():
     assert best == Tuning()
 
 
+def test_equal_settings_are_measured_once():
+    calls = []
+    best, table = descend(lambda t: calls.append(t) or 1.0, SPACE)
+    # Tuning() and the spelled-out default dense_min_flops=1024 are one setting
+    assert Tuning(dense_min_flops=1024) in table
+    assert len(calls) == len(table) - 1
+
+
 def test_descent_is_coordinate_wise():
     seen = []
 
@@ -37,4 +45,5 @@ def test_descent_is_coordinate_wise():
     assert best.dense_min_flops == 512
     # later knobs are tried on top of the best value found so far
     assert dataclasses.replace(best, hash_shift=1) in table
-    assert len(seen) == len(table) == 4   # default, 1024, 512, and 512 with hash_shift 1
+    # the default and its spelled-out dense_min_flops=1024 are measured once
+    assert len(table) == 4 and len(seen) == 3
