@@ -34,6 +34,9 @@ METRIC = "SpGEMM GFLOP/s + HBM-roofline %, learned/batched vs plain 2-phase, 1 G
 UNIT = "GFLOP/s"
 SCALE = 18
 L2_FLUSH_BYTES = 256 << 20
+FP64_LANES_PER_SM_CLK = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
 
 
 def peaks():
@@ -216,6 +219,10 @@ def run_ours(args):
     hbm, peak_src = peaks()
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
     traffic = profiled_traffic()
+    # the FP64 pipe: every product is one multiply and one add; GB300 issues
+    # 2 FP64 lanes per clock per SM (ncu peak_sustained of the FP64 pipe)
+    fp64_peak = FP64_LANES_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 1e9
+    fp64_achieved = 2.0 * flops_all / (num_avg * 1e-3) / 1e9 / world
 
     paths = run_paths(args, A, dA, sg, torch) if (rank == 0 and world == 1 and not args.no_paths) else None
     if paths is not None and not args.no_learned:
@@ -240,6 +247,11 @@ def run_ours(args):
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": peak_src,
                          "algorithmic_bytes": num_bytes, "traffic": traffic},
+            "fp64_roofline": {"bound": "alu", "kernel": "numeric phase (numeric_dense_kernel)",
+                              "achieved": round(fp64_achieved, 1), "peak": round(fp64_peak, 1),
+                              "unit": "G FP64 lane-ops/s (one mul + one add per product)",
+                              "frac": round(fp64_achieved / fp64_peak, 4),
+                              "peak_source": "2 FP64 lanes/clk/SM x 152 SMs x 2070 MHz"},
             "paths": paths,
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -270,7 +282,7 @@ def run_paths(args, A, dA, sg, torch):
     k=4 split + merge on the same product, 512 uneven ER products batched vs
     one by one, and the AMG Galerkin hierarchy in one CUDA graph vs the
     host-synced chain."""
-    from paper_1510_00844_gb300 import amg, inputs
+    from paper_1510_00844_gb300 import amg, autotune, inputs
     out = {}
     reps = 2
     flops = sg.plan(dA, dA).info()["flops"]
@@ -286,9 +298,11 @@ def run_paths(args, A, dA, sg, torch):
     _timed(torch, lambda: sg.batch_spgemm(As, Bs), 1)
     tb = _timed(torch, lambda: sg.batch_spgemm(As, Bs), reps)
     ts = _timed(torch, lambda: [sg.spgemm(a, b) for a, b in zip(As, Bs)], reps)
+    best, table = autotune.batch(As, Bs, repeats=2)
     out["batched_er512_f32"] = {"batched_ms": round(tb * 1e3, 3), "sequential_ms": round(ts * 1e3, 3),
                                 "speedup": round(ts / tb, 3), "flops": int(bflops),
-                                "gflops_batched": round(2 * bflops / tb / 1e9, 3)}
+                                "gflops_batched": round(2 * bflops / tb / 1e9, 3),
+                                "autotune": _tuning_report(best, table)}
     del As, Bs, pairs
     N = 128
     A0 = inputs.laplacian_7pt(N)
@@ -316,10 +330,19 @@ def run_paths(args, A, dA, sg, torch):
         T = sg.spgemm(Rt, A_)
         gflops += sg.plan(T, R).info()["flops"]
         A_ = sg.spgemm(T, R)
+    best, table = autotune.galerkin(dA0, dRs, s, repeats=5)
     out["amg_galerkin_128cubed_3levels"] = {"graph_ms": round(tg * 1e3, 3), "plain_ms": round(tp * 1e3, 3),
                                             "speedup": round(tp / tg, 3), "flops": int(gflops),
-                                            "gflops_graph": round(2 * gflops / tg / 1e9, 3)}
+                                            "gflops_graph": round(2 * gflops / tg / 1e9, 3),
+                                            "autotune": _tuning_report(best, table)}
     return out
+
+
+def _tuning_report(best, table):
+    """Chosen knobs, their time and the library default's (milliseconds)."""
+    from paper_1510_00844_gb300.spgemm import Tuning
+    return {"best": {k: v for k, v in vars(best).items() if v}, "best_ms": round(table[best], 3),
+            "default_ms": round(table[Tuning()], 3), "candidates": len(table)}
 
 
 def _checksum(torch, C):
