@@ -153,3 +153,23 @@ def test_amg_hierarchy_in_one_graph(sg, N, levels):
             assert np.array_equal(rp, L.rowptr) and np.array_equal(col, L.col)
             assert np.array_equal(val, L.val * 4.0 ** (l + 1))   # Galerkin closed form
             A = inputs.CSR(C.nrows, C.ncols, rp, col, val)
+
+
+def test_distributed_kslice_on_one_rank(sg, tmp_path):
+    """The k-split path of the multi-GPU module with the library's kernels on
+    a one-rank group: the exchange is empty, partial + merge give the product."""
+    import torch
+    import torch.distributed as dist
+    from paper_1510_00844_gb300 import distributed
+    store = dist.FileStore(str(tmp_path / "store"), 1)
+    dist.init_process_group("gloo", store=store, rank=0, world_size=1)
+    try:
+        A = inputs.rmat(11, seed=61)
+        dA = sg.to_device(A)
+        r0, r1, (rp, col, val) = distributed.gpu_kslice_product(dA, dA)
+        C = sg.spgemm(dA, dA)
+        assert (r0, r1) == (0, A.nrows)
+        assert bool((rp == C.rowptr).all()) and bool((col == C.col).all())
+        assert bool((val == C.val).all())
+    finally:
+        dist.destroy_process_group()
