@@ -447,7 +447,10 @@ def run_learned(args, sg, torch):
 
 def run_e2e(args, A, sg, torch, dev, dP):
     """Same metric through the public API from pinned host buffers: H2D of
-    A, plan + symbolic + numeric, D2H of C (row pointers, columns, values)."""
+    A, then C = A.A delivered to pinned host memory by row panels whose
+    device-to-host copies overlap the next panel's numeric phase
+    (pipeline.spgemm_to_host)."""
+    from paper_1510_00844_gb300 import pipeline
     if dP is None:
         return None
     hr = torch.from_numpy(A.rowptr).pin_memory()
@@ -468,26 +471,21 @@ def run_e2e(args, A, sg, torch, dev, dP):
         dc.copy_(hc, non_blocking=True)
         dv.copy_(hv, non_blocking=True)
         M = sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)
-        C = sg.spgemm(M, M)
-        if out_host is None:
-            out_host = (torch.empty(C.rowptr.numel(), dtype=torch.int64, pin_memory=True),
-                        torch.empty(C.col.numel(), dtype=C.col.dtype, pin_memory=True),
-                        torch.empty(C.val.numel(), dtype=torch.float64, pin_memory=True))
-        out_host[0].copy_(C.rowptr, non_blocking=True)
-        out_host[1].copy_(C.col, non_blocking=True)
-        out_host[2].copy_(C.val, non_blocking=True)
+        out_host = pipeline.spgemm_to_host(M, M, panels=8, out=out_host)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        d2h = C.rowptr.numel() * 8 + C.col.numel() * C.col.element_size() + C.val.numel() * 8
+        nnz = out_host.nnz
+        d2h = (A.nrows + 1) * 8 + nnz * (out_host.col.element_size() + 8)
         if it > 0:
             times.append(t1 - t0)
-        del C, M
+        del M
     fl = sg.plan(sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv),
                  sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)).info()["flops"]
     sec = float(np.mean(times))
     return {"value": round(2.0 * fl / sec / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": round(sec * 1e3, 3), "steps": nsteps}
+            "ms_per_step": round(sec * 1e3, 3), "steps": nsteps,
+            "note": "8 row panels, copies overlapped with the next panel's numeric phase"}
 
 
 def oracle_sample(A, target_flops):

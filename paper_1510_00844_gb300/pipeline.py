@@ -1,0 +1,116 @@
+"""C = A.B delivered to pinned host memory, one row panel at a time.
+
+A product whose C is read on the host pays for a device-to-host copy of
+every column index and value.  Here the rows of A are cut into panels.  The
+symbolic phase of all panels runs first, so that the host arrays can be
+sized once.  Then the numeric phase of panel p+1 runs on the compute stream
+while panel p's columns and values are copied to the host on copy streams.
+Two device buffers alternate between the two.  Panels also bound the device
+memory that C needs, so products whose C exceeds HBM can be formed (the row
+panelling of the learned-sizing workload)."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+import torch
+
+from . import spgemm as sg
+
+
+@dataclass
+class HostCSR:
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor          # int64 [nrows + 1], pinned host memory
+    col: torch.Tensor             # pinned host memory
+    val: Optional[torch.Tensor]   # pinned host memory, None for pattern-only
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def host_buffers(nrows: int, nnz: int, col_dtype, val_dtype) -> HostCSR:
+    """Pinned host arrays for a result; pass them back as `out` to reuse."""
+    return HostCSR(nrows, 0, torch.empty(nrows + 1, dtype=torch.int64, pin_memory=True),
+                   torch.empty(nnz, dtype=col_dtype, pin_memory=True),
+                   None if val_dtype is None else torch.empty(nnz, dtype=val_dtype,
+                                                              pin_memory=True))
+
+
+def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIMES,
+                   panels: int = 8, copy_streams: int = 2, out: Optional[HostCSR] = None,
+                   tuning: Optional[sg.Tuning] = None) -> HostCSR:
+    """C = A.B into pinned host memory (see the module docstring).  `out`
+    is reused when it is large enough; otherwise new buffers are pinned."""
+    dev = A.rowptr.device
+    m = A.nrows
+    panels = max(1, min(int(panels), max(m, 1)))
+    bounds = [((m * p) // panels, (m * (p + 1)) // panels) for p in range(panels)]
+    compute = torch.cuda.current_stream(dev)
+    plans: List[sg.Plan] = []
+    rowptrs: List[torch.Tensor] = []
+    counts: List[int] = []
+    for a, b in bounds:
+        end = A.rowend[a:b] if A.rowend is not None else A.rowptr[a + 1:b + 1]
+        view = sg.DeviceCSR(b - a, A.ncols, A.rowptr[a:b], A.col, A.val, rowend=end)
+        p = sg.plan(view, B, semiring, stream=compute, tuning=tuning)
+        rp, nnz = sg.symbolic(p)
+        plans.append(p)
+        rowptrs.append(rp)
+        counts.append(int(nnz))
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    total = int(offs[-1])
+    pattern = plans[0].pattern_only
+    col_dtype = A.col.dtype
+    val_dtype = None if pattern else A.val.dtype
+    if (out is None or out.col.numel() < total or out.rowptr.numel() < m + 1
+            or (val_dtype is not None and (out.val is None or out.val.numel() < total))):
+        out = host_buffers(m, total, col_dtype, val_dtype)
+    out.ncols = B.ncols
+    cap = max(counts) if counts else 0
+    bufs = []
+    for _ in range(min(2, panels)):
+        bufs.append((torch.empty(max(cap, 1), dtype=col_dtype, device=dev),
+                     None if pattern else torch.empty(max(cap, 1), dtype=val_dtype, device=dev)))
+    copiers = [torch.cuda.Stream(dev) for _ in range(max(1, copy_streams))]
+    free = [None] * len(bufs)            # event: the buffer's last copy finished
+    for p, (a, b) in enumerate(bounds):
+        k = p % len(bufs)
+        colb, valb = bufs[k]
+        if free[k] is not None:
+            compute.wait_event(free[k])
+        sg.numeric(plans[p], rowptrs[p], colb, valb)
+        rp_glob = rowptrs[p][1:] + int(offs[p])
+        ready = torch.cuda.Event()
+        ready.record(compute)
+        n = counts[p]
+        o = int(offs[p])
+        done = []
+        for j, s in enumerate(copiers):
+            s.wait_event(ready)
+            lo, hi = (n * j) // len(copiers), (n * (j + 1)) // len(copiers)
+            with torch.cuda.stream(s):
+                if hi > lo:
+                    out.col[o + lo:o + hi].copy_(colb[lo:hi], non_blocking=True)
+                    if valb is not None:
+                        out.val[o + lo:o + hi].copy_(valb[lo:hi], non_blocking=True)
+                if j == 0:
+                    out.rowptr[a + 1:b + 1].copy_(rp_glob, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
+                done.append(ev)
+        for ev in done[1:]:
+            copiers[0].wait_event(ev)
+        fin = torch.cuda.Event()
+        fin.record(copiers[0])
+        free[k] = fin
+        rp_glob.record_stream(copiers[0])
+    out.rowptr[0] = 0
+    for s in copiers:
+        s.synchronize()
+    for p in plans:
+        p.close()
+    return out

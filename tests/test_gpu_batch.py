@@ -173,3 +173,21 @@ def test_distributed_kslice_on_one_rank(sg, tmp_path):
         assert bool((val == C.val).all())
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("panels,semiring", [(1, 0), (3, 0), (8, 0), (5, 1)])
+def test_product_to_host_in_panels(sg, panels, semiring):
+    """Row panels computed one after another with the copy of each panel to
+    pinned host memory overlapping the next one's numeric phase: the host
+    arrays equal the device product."""
+    from paper_1510_00844_gb300 import pipeline
+    A = inputs.rmat(12, seed=71)
+    dA = sg.to_device(A)
+    H = pipeline.spgemm_to_host(dA, dA, semiring=semiring, panels=panels)
+    C = sg.spgemm(dA, dA, semiring=semiring)
+    assert np.array_equal(H.rowptr.numpy(), C.rowptr.cpu().numpy())
+    assert np.array_equal(H.col[:H.nnz].numpy(), C.col.cpu().numpy())
+    if semiring == 0:
+        assert np.array_equal(H.val[:H.nnz].numpy(), C.val.cpu().numpy())
+    H2 = pipeline.spgemm_to_host(dA, dA, semiring=semiring, panels=panels + 1, out=H)
+    assert H2 is H and np.array_equal(H2.col[:H2.nnz].numpy(), C.col.cpu().numpy())
