@@ -61,7 +61,22 @@ typedef enum {
 
 typedef enum { SPGEMM_F64 = 0, SPGEMM_F32 = 1, SPGEMM_I64 = 2, SPGEMM_BOOL = 3 } spgemm_value_type;
 typedef enum { SPGEMM_INDEX_I32 = 0, SPGEMM_INDEX_I64 = 1 } spgemm_index_type;
-typedef enum { SPGEMM_PLUS_TIMES = 0, SPGEMM_OR_AND = 1 } spgemm_semiring;
+/* Semirings (Sec. 2 states the product over a semiring):
+ *   PLUS_TIMES     (+, x) on the value type;
+ *   OR_AND         (or, and): the pattern only;
+ *   MIN_PLUS       (min, +): C(i,j) = min over k of A(i,k) + B(k,j);
+ *   MIN_SELECT2ND  (min, select2nd): C(i,j) = min over k of B(k,j)
+ *                  (the operations MIS-2 aggregation is built from, Alg. 3).
+ * The min semirings take float64 or int64 values (NOT_SUPPORTED otherwise);
+ * a min starts at +infinity (INT64_MAX) and keeps the running value unless a
+ * term is strictly smaller (a NaN term is never the minimum; the first of
+ * equal terms in ascending k is kept); int64 sums wrap around. */
+typedef enum {
+    SPGEMM_PLUS_TIMES = 0,
+    SPGEMM_OR_AND = 1,
+    SPGEMM_MIN_PLUS = 2,
+    SPGEMM_MIN_SELECT2ND = 3
+} spgemm_semiring;
 
 /* A CSR matrix in device memory.
  *   rowptr  int64[nrows+1]; row i spans [rowptr[i], rowptr[i+1]) ...

@@ -16,6 +16,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 F64, I64, BOOL = 0, 1, 2
+MINPLUS_F64, MINPLUS_I64, MINSEL_F64, MINSEL_I64 = 3, 4, 5, 6
+SEMIRINGS = ("plus_times", "or_and", "min_plus", "min_select2nd")
 
 
 class OCSR(NamedTuple):
@@ -86,17 +88,26 @@ def _p(a: Optional[np.ndarray]):
 
 
 def _vtype(val, semiring: str) -> int:
+    if semiring not in SEMIRINGS:
+        raise ValueError(f"unknown semiring {semiring}")
     if semiring == "or_and" or val is None:
         return BOOL
-    if np.issubdtype(val.dtype, np.integer):
-        return I64
-    return F64
+    integer = np.issubdtype(val.dtype, np.integer)
+    if semiring == "min_plus":
+        return MINPLUS_I64 if integer else MINPLUS_F64
+    if semiring == "min_select2nd":
+        return MINSEL_I64 if integer else MINSEL_F64
+    return I64 if integer else F64
+
+
+def _is_int(vt) -> bool:
+    return vt in (I64, MINPLUS_I64, MINSEL_I64)
 
 
 def _vals(val, vt):
     if vt == BOOL:
         return None
-    if vt == I64:
+    if _is_int(vt):
         return np.ascontiguousarray(val, dtype=np.int64)
     return np.ascontiguousarray(val, dtype=np.float64)   # float32 inputs are upcast
 
@@ -133,7 +144,7 @@ def spgemm(A, B, semiring: str = "plus_times", nthreads: int = 0) -> OCSR:
     rpC = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(cnt, out=rpC[1:])
     ciC = np.empty(nnz, dtype=np.int64)
-    vC = None if vt == BOOL else np.empty(nnz, dtype=np.int64 if vt == I64 else np.float64)
+    vC = None if vt == BOOL else np.empty(nnz, dtype=np.int64 if _is_int(vt) else np.float64)
     st = lib.oracle_spgemm_fill(m, n, _p(rpA), _p(ciA), _p(vA), _p(rpB), _p(ciB), _p(vB), vt,
                                 _p(rpC), _p(ciC), _p(vC), nthreads)
     if st != 0:
@@ -171,7 +182,7 @@ def sum_partials(parts: List, semiring: str = "plus_times", nthreads: int = 0) -
     rpC = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(cnt, out=rpC[1:])
     ciC = np.empty(nnz, dtype=np.int64)
-    vC = None if vt == BOOL else np.empty(nnz, dtype=np.int64 if vt == I64 else np.float64)
+    vC = None if vt == BOOL else np.empty(nnz, dtype=np.int64 if _is_int(vt) else np.float64)
     st = lib.oracle_sum_fill(c, m, n, ctypes.cast(rp_arr, ctypes.c_void_p),
                              ctypes.cast(ci_arr, ctypes.c_void_p),
                              None if v_arr is None else ctypes.cast(v_arr, ctypes.c_void_p), vt,

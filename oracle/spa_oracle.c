@@ -12,7 +12,14 @@
  *   ORACLE_F64   (+,x) on IEEE binary64, every product rounded, then added to
  *                the running sum (compiled with -ffp-contract=off: no FMA);
  *   ORACLE_I64   (+,x) on int64 with two's-complement wraparound;
- *   ORACLE_BOOL  (or,and) -- pattern only, no values.
+ *   ORACLE_BOOL  (or,and) -- pattern only, no values;
+ *   ORACLE_MINPLUS_F64 / _I64    (min,+): C(i,j) = min over k of A(i,k)+B(k,j)
+ *                (binary64 sums rounded; int64 sums wrap around);
+ *   ORACLE_MINSEL_F64 / _I64     (min,select2nd): C(i,j) = min over k of B(k,j)
+ *                (the operations MIS-2 aggregation is built from, Alg. 3).
+ * A min reduction starts from its identity (+infinity, INT64_MAX) and keeps
+ * the running value x unless the next term y satisfies y < x, so a NaN term
+ * never becomes the minimum and the first of equal terms is kept.
  *
  * The method is Gustavson's (Alg. 1, written column-wise in the paper; here
  * row-wise over CSR, the same algorithm on the transposed problem) with a
@@ -39,7 +46,50 @@
 #include <omp.h>
 #endif
 
-enum { ORACLE_F64 = 0, ORACLE_I64 = 1, ORACLE_BOOL = 2 };
+enum {
+    ORACLE_F64 = 0,
+    ORACLE_I64 = 1,
+    ORACLE_BOOL = 2,
+    ORACLE_MINPLUS_F64 = 3,
+    ORACLE_MINPLUS_I64 = 4,
+    ORACLE_MINSEL_F64 = 5,
+    ORACLE_MINSEL_I64 = 6
+};
+
+static int is_f64(int vt) {
+    return vt == ORACLE_F64 || vt == ORACLE_MINPLUS_F64 || vt == ORACLE_MINSEL_F64;
+}
+static int is_i64(int vt) {
+    return vt == ORACLE_I64 || vt == ORACLE_MINPLUS_I64 || vt == ORACLE_MINSEL_I64;
+}
+static int is_min(int vt) { return vt >= ORACLE_MINPLUS_F64; }
+
+/* a (x) b of the semiring */
+static double mul_d(int vt, double a, double b) {
+    if (vt == ORACLE_MINPLUS_F64) return a + b;
+    if (vt == ORACLE_MINSEL_F64) return b;
+    return a * b;
+}
+static uint64_t mul_i(int vt, uint64_t a, uint64_t b) {
+    if (vt == ORACLE_MINPLUS_I64) return a + b;
+    if (vt == ORACLE_MINSEL_I64) return b;
+    return a * b;
+}
+/* running (+) of the semiring; `first` starts from the identity */
+static double add_d(int vt, int first, double x, double y) {
+    if (is_min(vt)) {
+        if (first) x = 1.0 / 0.0;
+        return y < x ? y : x;
+    }
+    return first ? y : x + y;
+}
+static uint64_t add_i(int vt, int first, uint64_t x, uint64_t y) {
+    if (is_min(vt)) {
+        int64_t sx = first ? INT64_MAX : (int64_t)x, sy = (int64_t)y;
+        return (uint64_t)(sy < sx ? sy : sx);
+    }
+    return first ? y : x + y;
+}
 
 static int cmp_i64(const void* a, const void* b) {
     int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
@@ -126,9 +176,9 @@ int oracle_spgemm_fill(int64_t m, int64_t n, const int64_t* rpA, const int64_t* 
         int64_t* list = (int64_t*)malloc(sizeof(int64_t) * nn);
         double* spa_d = NULL;
         uint64_t* spa_i = NULL;
-        if (vtype == ORACLE_F64) spa_d = (double*)malloc(sizeof(double) * nn);
-        if (vtype == ORACLE_I64) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
-        if (!stamp || !list || (vtype == ORACLE_F64 && !spa_d) || (vtype == ORACLE_I64 && !spa_i)) {
+        if (is_f64(vtype)) spa_d = (double*)malloc(sizeof(double) * nn);
+        if (is_i64(vtype)) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
+        if (!stamp || !list || (is_f64(vtype) && !spa_d) || (is_i64(vtype) && !spa_i)) {
 #pragma omp atomic write
             status = -1;
         } else {
@@ -151,12 +201,12 @@ int oracle_spgemm_fill(int64_t m, int64_t n, const int64_t* rpA, const int64_t* 
                             stamp[j] = i;
                             list[nz++] = j;
                         }
-                        if (vtype == ORACLE_F64) {
-                            double prod = aD[p] * bD[q];
-                            spa_d[j] = first ? prod : spa_d[j] + prod;
-                        } else if (vtype == ORACLE_I64) {
-                            uint64_t prod = aI[p] * bI[q];
-                            spa_i[j] = first ? prod : spa_i[j] + prod;
+                        if (is_f64(vtype)) {
+                            double prod = mul_d(vtype, aD[p], bD[q]);
+                            spa_d[j] = add_d(vtype, first, spa_d[j], prod);
+                        } else if (is_i64(vtype)) {
+                            uint64_t prod = mul_i(vtype, aI[p], bI[q]);
+                            spa_i[j] = add_i(vtype, first, spa_i[j], prod);
                         }
                     }
                 }
@@ -170,8 +220,8 @@ int oracle_spgemm_fill(int64_t m, int64_t n, const int64_t* rpA, const int64_t* 
                 for (int64_t t = 0; t < nz; ++t) {
                     int64_t j = list[t];
                     ciC[base + t] = j;
-                    if (vtype == ORACLE_F64) cD[base + t] = spa_d[j];
-                    else if (vtype == ORACLE_I64) cI[base + t] = spa_i[j];
+                    if (is_f64(vtype)) cD[base + t] = spa_d[j];
+                    else if (is_i64(vtype)) cI[base + t] = spa_i[j];
                 }
             }
         }
@@ -230,9 +280,9 @@ int oracle_sum_fill(int c, int64_t m, int64_t n, const int64_t* const* rps,
         int64_t* list = (int64_t*)malloc(sizeof(int64_t) * nn);
         double* spa_d = NULL;
         uint64_t* spa_i = NULL;
-        if (vtype == ORACLE_F64) spa_d = (double*)malloc(sizeof(double) * nn);
-        if (vtype == ORACLE_I64) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
-        if (!stamp || !list || (vtype == ORACLE_F64 && !spa_d) || (vtype == ORACLE_I64 && !spa_i)) {
+        if (is_f64(vtype)) spa_d = (double*)malloc(sizeof(double) * nn);
+        if (is_i64(vtype)) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
+        if (!stamp || !list || (is_f64(vtype) && !spa_d) || (is_i64(vtype) && !spa_i)) {
 #pragma omp atomic write
             status = -1;
         } else {
@@ -252,8 +302,8 @@ int oracle_sum_fill(int c, int64_t m, int64_t n, const int64_t* const* rps,
                             stamp[j] = i;
                             list[nz++] = j;
                         }
-                        if (vtype == ORACLE_F64) spa_d[j] = first ? vd[q] : spa_d[j] + vd[q];
-                        else if (vtype == ORACLE_I64) spa_i[j] = first ? vi[q] : spa_i[j] + vi[q];
+                        if (is_f64(vtype)) spa_d[j] = add_d(vtype, first, spa_d[j], vd[q]);
+                        else if (is_i64(vtype)) spa_i[j] = add_i(vtype, first, spa_i[j], vi[q]);
                     }
                 }
                 if (nz != rpC[i + 1] - rpC[i]) {
@@ -266,8 +316,8 @@ int oracle_sum_fill(int c, int64_t m, int64_t n, const int64_t* const* rps,
                 for (int64_t t = 0; t < nz; ++t) {
                     int64_t j = list[t];
                     ciC[base + t] = j;
-                    if (vtype == ORACLE_F64) cD[base + t] = spa_d[j];
-                    else if (vtype == ORACLE_I64) cI[base + t] = spa_i[j];
+                    if (is_f64(vtype)) cD[base + t] = spa_d[j];
+                    else if (is_i64(vtype)) cI[base + t] = spa_i[j];
                 }
             }
         }

@@ -61,7 +61,21 @@ spgemm_status check_csr(const spgemm_csr* M, const char* name, bool need_vals) {
 // value type the kernels use: BOOL for the (or, and) semiring
 int kernel_value_type(const spgemm_csr* A, const spgemm_opts* o) {
     if ((o && o->semiring == SPGEMM_OR_AND) || A->value_type == SPGEMM_BOOL) return SPGEMM_BOOL;
+    if (o && o->semiring == SPGEMM_MIN_PLUS)
+        return A->value_type == SPGEMM_I64 ? sg::kVtMinPlusI64 : sg::kVtMinPlusF64;
+    if (o && o->semiring == SPGEMM_MIN_SELECT2ND)
+        return A->value_type == SPGEMM_I64 ? sg::kVtMinSelI64 : sg::kVtMinSelF64;
     return A->value_type;
+}
+
+// The min semirings run on float64 and int64 values only.
+spgemm_status check_semiring(const spgemm_opts& o, const spgemm_csr* A) {
+    if (o.semiring < SPGEMM_PLUS_TIMES || o.semiring > SPGEMM_MIN_SELECT2ND)
+        return fail(SPGEMM_ERR_INVALID_ARG, "unknown semiring %d", o.semiring);
+    if ((o.semiring == SPGEMM_MIN_PLUS || o.semiring == SPGEMM_MIN_SELECT2ND) && A &&
+        A->value_type != SPGEMM_F64 && A->value_type != SPGEMM_I64)
+        return fail(SPGEMM_ERR_NOT_SUPPORTED, "the min semirings need float64 or int64 values");
+    return SPGEMM_OK;
 }
 
 int device_sm_count(int* smem_optin) {
@@ -137,8 +151,8 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     if (count < 1) return fail(SPGEMM_ERR_INVALID_ARG, "a batch needs at least one product");
     spgemm_opts o{};
     if (opts) o = *opts;
-    if (o.semiring != SPGEMM_PLUS_TIMES && o.semiring != SPGEMM_OR_AND)
-        return fail(SPGEMM_ERR_INVALID_ARG, "unknown semiring %d", o.semiring);
+    if (!A || !B) return fail(SPGEMM_ERR_INVALID_ARG, "A or B is NULL");
+    if (spgemm_status st0 = check_semiring(o, &A[0]); st0 != SPGEMM_OK) return st0;
     if (o.dense_chunk != 0 && o.dense_chunk != sg::kDenseW0 && o.dense_chunk != sg::kDenseW1)
         return fail(SPGEMM_ERR_INVALID_ARG, "dense_chunk must be 0, %d or %d", sg::kDenseW0,
                     sg::kDenseW1);
@@ -201,7 +215,7 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
     P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;
     {
-        const size_t vbytes = vt == SPGEMM_F64 || vt == SPGEMM_I64 ? 8 : vt == SPGEMM_F32 ? 4 : 0;
+        const size_t vbytes = sg::vt_bytes(vt);
         int cfg = (vbytes == 8) ? 0 : 1;
         if (o.dense_chunk == sg::kDenseW0) cfg = 0;
         if (o.dense_chunk == sg::kDenseW1) cfg = 1;
@@ -278,16 +292,10 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
 
     auto prepare = [&]() -> cudaError_t {
         const bool i32 = P->it == SPGEMM_INDEX_I32;
-        switch (P->vt) {
-            case SPGEMM_F64:
-                return i32 ? sg::prepare_numeric<int32_t, double>(*P) : sg::prepare_numeric<int64_t, double>(*P);
-            case SPGEMM_F32:
-                return i32 ? sg::prepare_numeric<int32_t, float>(*P) : sg::prepare_numeric<int64_t, float>(*P);
-            case SPGEMM_I64:
-                return i32 ? sg::prepare_numeric<int32_t, int64_t>(*P) : sg::prepare_numeric<int64_t, int64_t>(*P);
-            default:
-                return i32 ? sg::prepare_numeric<int32_t, sg::NoVal>(*P) : sg::prepare_numeric<int64_t, sg::NoVal>(*P);
-        }
+        return sg::with_value_type(P->vt, [&](auto tag) -> cudaError_t {
+            using V = decltype(tag);
+            return i32 ? sg::prepare_numeric<int32_t, V>(*P) : sg::prepare_numeric<int64_t, V>(*P);
+        });
     };
 
     if (device_sized) {
@@ -375,20 +383,12 @@ spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes) {
 cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long long cap,
                         void* colC, void* valC) {
     const bool i32 = P->it == SPGEMM_INDEX_I32;
-    switch (P->vt) {
-        case SPGEMM_F64:
-            return i32 ? sg::launch_numeric<int32_t, double>(*P, w, rowptrC, cap, colC, valC)
-                       : sg::launch_numeric<int64_t, double>(*P, w, rowptrC, cap, colC, valC);
-        case SPGEMM_F32:
-            return i32 ? sg::launch_numeric<int32_t, float>(*P, w, rowptrC, cap, colC, valC)
-                       : sg::launch_numeric<int64_t, float>(*P, w, rowptrC, cap, colC, valC);
-        case SPGEMM_I64:
-            return i32 ? sg::launch_numeric<int32_t, int64_t>(*P, w, rowptrC, cap, colC, valC)
-                       : sg::launch_numeric<int64_t, int64_t>(*P, w, rowptrC, cap, colC, valC);
-        default:
-            return i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, w, rowptrC, cap, colC, nullptr)
-                       : sg::launch_numeric<int64_t, sg::NoVal>(*P, w, rowptrC, cap, colC, nullptr);
-    }
+    return sg::with_value_type(P->vt, [&](auto tag) -> cudaError_t {
+        using V = decltype(tag);
+        void* vals = VOps<V>::has_val ? valC : nullptr;
+        return i32 ? sg::launch_numeric<int32_t, V>(*P, w, rowptrC, cap, colC, vals)
+                   : sg::launch_numeric<int64_t, V>(*P, w, rowptrC, cap, colC, vals);
+    });
 }
 
 }  // namespace sg
@@ -587,6 +587,7 @@ static spgemm_status check_parts(int32_t c, const spgemm_csr* parts, const spgem
     if (!parts) return fail(SPGEMM_ERR_INVALID_ARG, "parts is NULL");
     spgemm_opts o{};
     if (opts) o = *opts;
+    if (spgemm_status st0 = check_semiring(o, &parts[0]); st0 != SPGEMM_OK) return st0;
     const int vt = kernel_value_type(&parts[0], &o);
     for (int s = 0; s < c; ++s) {
         spgemm_status st = check_csr(&parts[s], "part", vt != SPGEMM_BOOL);

@@ -5,6 +5,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 namespace sg {
@@ -124,10 +126,77 @@ struct VOps<NoVal> {  // (or, and): pattern only
     __device__ static __forceinline__ NoVal add(NoVal, NoVal) { return {}; }
 };
 
+// The (min, +) and (min, select2nd) semirings (the operations MIS-2
+// aggregation is built from, Alg. 3), stored as plain double / int64 values.
+// A min reduction starts at its identity (+infinity, INT64_MAX) and keeps the
+// running value x unless the next term y satisfies y < x, so a NaN term is
+// never the minimum and the first of equal terms is kept; the result does not
+// depend on the order of the terms except through that first-kept rule, and
+// every path adds terms in ascending k (ascending slice for the merge).
+template <class T>
+struct MinPlus {
+    T x;
+};
+template <class T>
+struct MinSel {
+    T x;
+};
+
+template <>
+struct VOps<MinPlus<double>> {
+    static constexpr bool has_val = true;
+    __device__ static __forceinline__ MinPlus<double> init() {
+        return {__longlong_as_double(0x7ff0000000000000LL)};
+    }
+    __device__ static __forceinline__ MinPlus<double> mul(MinPlus<double> a, MinPlus<double> b) {
+        return {__dadd_rn(a.x, b.x)};
+    }
+    __device__ static __forceinline__ MinPlus<double> add(MinPlus<double> s, MinPlus<double> t) {
+        return {t.x < s.x ? t.x : s.x};
+    }
+};
+
+template <>
+struct VOps<MinPlus<int64_t>> {  // sums wrap around (two's complement)
+    static constexpr bool has_val = true;
+    __device__ static __forceinline__ MinPlus<int64_t> init() { return {INT64_MAX}; }
+    __device__ static __forceinline__ MinPlus<int64_t> mul(MinPlus<int64_t> a, MinPlus<int64_t> b) {
+        return {(int64_t)((unsigned long long)a.x + (unsigned long long)b.x)};
+    }
+    __device__ static __forceinline__ MinPlus<int64_t> add(MinPlus<int64_t> s, MinPlus<int64_t> t) {
+        return {t.x < s.x ? t.x : s.x};
+    }
+};
+
+template <class T>
+struct VOps<MinSel<T>> {
+    static constexpr bool has_val = true;
+    __device__ static __forceinline__ MinSel<T> init() {
+        if constexpr (std::is_floating_point<T>::value)
+            return {__longlong_as_double(0x7ff0000000000000LL)};
+        else
+            return {INT64_MAX};
+    }
+    __device__ static __forceinline__ MinSel<T> mul(MinSel<T>, MinSel<T> b) { return b; }
+    __device__ static __forceinline__ MinSel<T> add(MinSel<T> s, MinSel<T> t) {
+        return {t.x < s.x ? t.x : s.x};
+    }
+};
+
 template <class V>
 __device__ __forceinline__ V shfl_val(V v, int src) {
     if constexpr (VOps<V>::has_val) return __shfl_sync(kFull, v, src);
     else return v;
+}
+
+template <class T>
+__device__ __forceinline__ MinPlus<T> shfl_val(MinPlus<T> v, int src) {
+    return {__shfl_sync(kFull, v.x, src)};
+}
+
+template <class T>
+__device__ __forceinline__ MinSel<T> shfl_val(MinSel<T> v, int src) {
+    return {__shfl_sync(kFull, v.x, src)};
 }
 
 template <class V>

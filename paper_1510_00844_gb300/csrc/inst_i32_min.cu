@@ -1,0 +1,9 @@
+// Instantiations of the numeric launchers for the (min, +) and
+// (min, select2nd) semirings, int32_t column indices.
+#include "launch.cuh"
+namespace sg {
+SG_INSTANTIATE_IT_V(int32_t, MinPlus<double>)
+SG_INSTANTIATE_IT_V(int32_t, MinPlus<int64_t>)
+SG_INSTANTIATE_IT_V(int32_t, MinSel<double>)
+SG_INSTANTIATE_IT_V(int32_t, MinSel<int64_t>)
+}

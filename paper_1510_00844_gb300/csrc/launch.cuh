@@ -292,4 +292,15 @@ cudaError_t launch_dense_slot_pack(Plan& P, const int64_t* rpC, void* colC, void
                                                    int32_t*, unsigned*);                       \
     template cudaError_t launch_row_features<IT>(Plan&, float*);
 
+// The numeric launchers of one value type (used for the min semirings, which
+// are instantiated in their own translation units so they compile in
+// parallel with the others).
+#define SG_INSTANTIATE_IT_V(IT, V)                                                              \
+    template cudaError_t prepare_numeric<IT, V>(Plan&);                                        \
+    template cudaError_t launch_numeric<IT, V>(Plan&, unsigned char*, const int64_t*,          \
+                                               long long, void*, void*, int64_t*, int32_t*,    \
+                                               unsigned*);                                     \
+    template cudaError_t launch_dense_slot_pack<IT, V>(Plan&, const int64_t*, void*, void*,    \
+                                                       int64_t*);
+
 }  // namespace sg

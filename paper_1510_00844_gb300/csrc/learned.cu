@@ -161,7 +161,7 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
         ~Guard() { spgemm_plan_destroy(p); }
     } guard{P};
     const size_t isz = P->it == SPGEMM_INDEX_I32 ? 4 : 8;
-    const size_t vsz = P->vt == SPGEMM_F64 || P->vt == SPGEMM_I64 ? 8 : P->vt == SPGEMM_F32 ? 4 : 0;
+    const size_t vsz = sg::vt_bytes(P->vt);
     sg::WsLayout L = sg::workspace_layout(*P);
     unsigned char* ws = get(L.total + al(sizeof(unsigned)) + al((size_t)m * 4) + al((size_t)m * 4));
     if (!ws) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
@@ -196,45 +196,21 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
     if (e == cudaSuccess && m > 0) e = cudaMemsetAsync(rowend, 0, (size_t)m * 8, s);
     if (e == cudaSuccess) {
         const bool i32 = P->it == SPGEMM_INDEX_I32;
-        switch (P->vt) {
-            case SPGEMM_F64:
-                e = i32 ? sg::launch_numeric<int32_t, double>(*P, ws, slots, total, col, val, rowend, olist, ocount)
-                        : sg::launch_numeric<int64_t, double>(*P, ws, slots, total, col, val, rowend, olist, ocount);
-                break;
-            case SPGEMM_F32:
-                e = i32 ? sg::launch_numeric<int32_t, float>(*P, ws, slots, total, col, val, rowend, olist, ocount)
-                        : sg::launch_numeric<int64_t, float>(*P, ws, slots, total, col, val, rowend, olist, ocount);
-                break;
-            case SPGEMM_I64:
-                e = i32 ? sg::launch_numeric<int32_t, int64_t>(*P, ws, slots, total, col, val, rowend, olist, ocount)
-                        : sg::launch_numeric<int64_t, int64_t>(*P, ws, slots, total, col, val, rowend, olist, ocount);
-                break;
-            default:
-                e = i32 ? sg::launch_numeric<int32_t, sg::NoVal>(*P, ws, slots, total, col, nullptr, rowend, olist, ocount)
-                        : sg::launch_numeric<int64_t, sg::NoVal>(*P, ws, slots, total, col, nullptr, rowend, olist, ocount);
-                break;
-        }
+        e = sg::with_value_type(P->vt, [&](auto tag) -> cudaError_t {
+            using V = decltype(tag);
+            void* vv = sg::VOps<V>::has_val ? (void*)val : nullptr;
+            return i32 ? sg::launch_numeric<int32_t, V>(*P, ws, slots, total, col, vv, rowend, olist, ocount)
+                       : sg::launch_numeric<int64_t, V>(*P, ws, slots, total, col, vv, rowend, olist, ocount);
+        });
     }
     if (e == cudaSuccess && P->ndense > 0) {
         const bool i32 = P->it == SPGEMM_INDEX_I32;
-        switch (P->vt) {
-            case SPGEMM_F64:
-                e = i32 ? sg::launch_dense_slot_pack<int32_t, double>(*P, slots, col, val, rowend)
-                        : sg::launch_dense_slot_pack<int64_t, double>(*P, slots, col, val, rowend);
-                break;
-            case SPGEMM_F32:
-                e = i32 ? sg::launch_dense_slot_pack<int32_t, float>(*P, slots, col, val, rowend)
-                        : sg::launch_dense_slot_pack<int64_t, float>(*P, slots, col, val, rowend);
-                break;
-            case SPGEMM_I64:
-                e = i32 ? sg::launch_dense_slot_pack<int32_t, int64_t>(*P, slots, col, val, rowend)
-                        : sg::launch_dense_slot_pack<int64_t, int64_t>(*P, slots, col, val, rowend);
-                break;
-            default:
-                e = i32 ? sg::launch_dense_slot_pack<int32_t, sg::NoVal>(*P, slots, col, nullptr, rowend)
-                        : sg::launch_dense_slot_pack<int64_t, sg::NoVal>(*P, slots, col, nullptr, rowend);
-                break;
-        }
+        e = sg::with_value_type(P->vt, [&](auto tag) -> cudaError_t {
+            using V = decltype(tag);
+            void* vv = sg::VOps<V>::has_val ? (void*)val : nullptr;
+            return i32 ? sg::launch_dense_slot_pack<int32_t, V>(*P, slots, col, vv, rowend)
+                       : sg::launch_dense_slot_pack<int64_t, V>(*P, slots, col, vv, rowend);
+        });
     }
     if (e == cudaSuccess && m > 0) {
         const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>((m + 255) / 256, (long long)P->sm_count * 8));
@@ -334,24 +310,16 @@ spgemm_status spgemm_learned_multiply(const spgemm_csr* A, const spgemm_csr* B,
     unsigned char* val_f = vsz ? get((size_t)nnz * vsz) : nullptr;
     if (!col_f || (vsz && !val_f)) return lfail(SPGEMM_ERR_OUT_OF_MEMORY, "allocation callback failed");
     const bool i32 = P->it == SPGEMM_INDEX_I32;
-    switch (P->vt) {
-        case SPGEMM_F64:
-            e = i32 ? sg::launch_compact<int32_t, double>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f)
-                    : sg::launch_compact<int64_t, double>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f);
-            break;
-        case SPGEMM_F32:
-            e = i32 ? sg::launch_compact<int32_t, float>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f)
-                    : sg::launch_compact<int64_t, float>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f);
-            break;
-        case SPGEMM_I64:
-            e = i32 ? sg::launch_compact<int32_t, int64_t>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f)
-                    : sg::launch_compact<int64_t, int64_t>(m, P->sm_count, s, slots, inv, rp_x, col, val, col_x, val_x, rp_f, col_f, val_f);
-            break;
-        default:
-            e = i32 ? sg::launch_compact<int32_t, sg::NoVal>(m, P->sm_count, s, slots, inv, rp_x, col, nullptr, col_x, nullptr, rp_f, col_f, nullptr)
-                    : sg::launch_compact<int64_t, sg::NoVal>(m, P->sm_count, s, slots, inv, rp_x, col, nullptr, col_x, nullptr, rp_f, col_f, nullptr);
-            break;
-    }
+    e = sg::with_value_type(P->vt, [&](auto tag) -> cudaError_t {
+        using V = decltype(tag);
+        const bool hv = sg::VOps<V>::has_val;
+        return i32 ? sg::launch_compact<int32_t, V>(m, P->sm_count, s, slots, inv, rp_x, col,
+                                                    hv ? val : nullptr, col_x, hv ? val_x : nullptr,
+                                                    rp_f, col_f, hv ? val_f : nullptr)
+                   : sg::launch_compact<int64_t, V>(m, P->sm_count, s, slots, inv, rp_x, col,
+                                                    hv ? val : nullptr, col_x, hv ? val_x : nullptr,
+                                                    rp_f, col_f, hv ? val_f : nullptr);
+    });
     if (e != cudaSuccess) return lcuda(e, "learned: compaction");
     out->rowptr = rp_f;
     out->rowend = nullptr;

@@ -159,12 +159,10 @@ cudaError_t launch_merge(int c, const spgemm_csr* parts, int vt, long long m, lo
                                                               rowcnt, rpC, colC, valC, err)      \
                           : launch_merge_t<int64_t, V, false>(c, parts, m, n, sm_count, s,       \
                                                               rowcnt, rpC, colC, valC, err));
-    switch (vt) {
-        case SPGEMM_F64: SG_MERGE_CASE(double)
-        case SPGEMM_F32: SG_MERGE_CASE(float)
-        case SPGEMM_I64: SG_MERGE_CASE(int64_t)
-        default: SG_MERGE_CASE(NoVal)
-    }
+    return with_value_type(vt, [&](auto tag) -> cudaError_t {
+        using V = decltype(tag);
+        SG_MERGE_CASE(V)
+    });
 #undef SG_MERGE_CASE
 }
 

@@ -61,6 +61,30 @@ using Plan = spgemm_plan_s;
 
 namespace sg {
 
+// Value kinds of the kernels: the storage types of spgemm_value_type (BOOL
+// when only the pattern is computed) and the min semirings on double and
+// int64 storage.
+constexpr int kVtMinPlusF64 = 16, kVtMinPlusI64 = 17, kVtMinSelF64 = 18, kVtMinSelI64 = 19;
+
+inline size_t vt_bytes(int vt) {
+    return vt == SPGEMM_F32 ? 4 : vt == SPGEMM_BOOL ? 0 : 8;
+}
+
+// Calls f(V{}) with the value type of kind vt.
+template <class F>
+decltype(auto) with_value_type(int vt, F&& f) {
+    switch (vt) {
+        case SPGEMM_F64: return f(double{});
+        case SPGEMM_F32: return f(float{});
+        case SPGEMM_I64: return f(int64_t{});
+        case kVtMinPlusF64: return f(MinPlus<double>{});
+        case kVtMinPlusI64: return f(MinPlus<int64_t>{});
+        case kVtMinSelF64: return f(MinSel<double>{});
+        case kVtMinSelI64: return f(MinSel<int64_t>{});
+        default: return f(NoVal{});
+    }
+}
+
 // Process-wide count of kernels this library has launched.
 void count_launches(long long k);
 // Message returned by spgemm_last_error() on this thread.

@@ -23,7 +23,7 @@ from . import build as _build
 
 F64, F32, I64, BOOL = 0, 1, 2, 3
 INDEX_I32, INDEX_I64 = 0, 1
-PLUS_TIMES, OR_AND = 0, 1
+PLUS_TIMES, OR_AND, MIN_PLUS, MIN_SELECT2ND = 0, 1, 2, 3
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_CSR", 3: "INDEX_OVERFLOW", 4: "OUT_OF_MEMORY",
           5: "TIMEOUT", 6: "CUDA", 7: "NOT_SUPPORTED", 8: "INTERNAL"}

@@ -293,3 +293,93 @@ def test_mcl_prune_renorm():
         assert np.array_equal(Q.col[a:b], np.asarray(P.col[P.rowptr[i]:P.rowptr[i + 1]])[sel])
         if b > a:
             assert abs(Q.val[a:b].sum() - 1.0) <= 1e-13
+
+
+# ------------------------------------------------------------ min semirings
+# (min, +) and (min, select2nd): the operations MIS-2 aggregation is built
+# from (Alg. 3).  A min reduction starts at +inf (int64: INT64_MAX) and keeps
+# the running value unless the next term is strictly smaller.
+
+def brute_min(A, B, select2nd: bool):
+    """Pure-Python triple loop over structural nonzeros, k ascending."""
+    integer = np.issubdtype(np.asarray(A.val).dtype, np.integer)
+    ident = np.iinfo(np.int64).max if integer else float("inf")
+    out = {}
+    for i in range(A.nrows):
+        for p in range(A.rowptr[i], A.rowptr[i + 1]):
+            k = int(A.col[p])
+            for q in range(B.rowptr[k], B.rowptr[k + 1]):
+                j = int(B.col[q])
+                a, b = A.val[p], B.val[q]
+                term = b if select2nd else (int(a) + int(b) if integer else float(a) + float(b))
+                cur = out.get((i, j), ident)
+                out[(i, j)] = term if term < cur else cur
+    return out
+
+
+@pytest.mark.parametrize("select2nd", [False, True])
+@pytest.mark.parametrize("value", ["u01_f64", "int"])
+@pytest.mark.parametrize("seed", range(3))
+def test_min_semirings_against_brute_force(select2nd, value, seed):
+    A = inputs.random_csr(11, 14, 0.35, 300 + seed, value=value)
+    B = inputs.random_csr(14, 9, 0.35, 400 + seed, value=value)
+    sr = "min_select2nd" if select2nd else "min_plus"
+    C = oracle.spgemm(A, B, semiring=sr)
+    assert_valid_csr(C)
+    ref = brute_min(A, B, select2nd)
+    got = {}
+    for i in range(C.nrows):
+        for t in range(C.rowptr[i], C.rowptr[i + 1]):
+            got[(i, int(C.col[t]))] = C.val[t]
+    assert got.keys() == ref.keys()
+    assert all(got[key] == ref[key] for key in ref)
+    # the pattern is the structural product, as for every semiring
+    assert np.array_equal(pattern(C), (pattern(A).astype(int) @ pattern(B).astype(int)) > 0)
+
+
+def test_min_plus_path_graph_closed_form():
+    """Path graph 0-1-...-(n-1) with unit weights: (min,+) square gives
+    distance-2 walks: C(i,i) = 2 for every vertex with a neighbour, C(i,i+-2)
+    = 2, nothing else."""
+    n = 12
+    rows = np.concatenate([np.arange(n - 1), np.arange(1, n)])
+    cols = np.concatenate([np.arange(1, n), np.arange(n - 1)])
+    W = inputs.coo_to_csr(n, n, rows, cols, np.ones(rows.size))
+    C = oracle.spgemm(W, W, semiring="min_plus")
+    D = dense(C)
+    for i in range(n):
+        for j in range(n):
+            expect = 2.0 if (i == j or abs(i - j) == 2) else 0.0
+            assert D[i, j] == expect, (i, j)
+
+
+def test_min_semiring_identity_and_selection():
+    """I (zero weights) (min,+) B = B; A (min,select2nd) B takes the minimum
+    of the rows of B that A selects (numpy reduction per row)."""
+    B = inputs.random_csr(20, 15, 0.3, 9, value="u01_f64")
+    Z = inputs.CSR(20, 20, np.arange(21, dtype=np.int64), np.arange(20, dtype=np.int64),
+                   np.zeros(20))
+    C = oracle.spgemm(Z, B, semiring="min_plus")
+    assert np.array_equal(C.rowptr, B.rowptr) and np.array_equal(C.col, B.col)
+    assert np.array_equal(C.val, B.val)
+    A = inputs.random_csr(7, 20, 0.25, 10, value="u01_f64")
+    S = oracle.spgemm(A, B, semiring="min_select2nd")
+    DB = np.where(pattern(B), dense(B), np.inf)
+    for i in range(A.nrows):
+        ks = np.asarray(A.col[A.rowptr[i]:A.rowptr[i + 1]], dtype=np.int64)
+        expect = DB[ks].min(axis=0) if ks.size else np.full(B.ncols, np.inf)
+        row = np.full(B.ncols, np.inf)
+        row[np.asarray(S.col[S.rowptr[i]:S.rowptr[i + 1]], dtype=np.int64)] = \
+            S.val[S.rowptr[i]:S.rowptr[i + 1]]
+        assert np.array_equal(row, expect)
+
+
+@pytest.mark.parametrize("sr", ["min_plus", "min_select2nd"])
+@pytest.mark.parametrize("c", [2, 5])
+def test_min_merge_of_kslices_equals_unsplit(sr, c):
+    A = inputs.rmat(9, seed=33, value="u01_f64")
+    full = oracle.spgemm(A, A, semiring=sr)
+    parts = [oracle.spgemm(As, Bs, semiring=sr) for As, Bs in oracle.kslice(A, A, c)]
+    M = oracle.sum_partials(parts, semiring=sr)
+    assert np.array_equal(M.rowptr, full.rowptr) and np.array_equal(M.col, full.col)
+    assert np.array_equal(M.val, full.val)      # min keeps the first of equal terms
