@@ -307,6 +307,23 @@ spgemm_status spgemm_transpose(const spgemm_csr* A, void* stream, void* ws, size
  * spgemm_mcl_workspace_size(m) bytes, 256-byte aligned, kept between the two
  * calls. */
 size_t spgemm_mcl_workspace_size(int64_t m);
+
+/* ---- masked product (the structural mask MIS-2 applies to its semiring
+ *      products, Alg. 3) ----
+ * Keeps the entries (i, j) of C that are in the pattern of M (complement =
+ * 0) or not in it (complement != 0).  C and M: same shape and index type,
+ * rows sorted ascending; either may be a view (rowend).  The mask is applied
+ * to the finished product (the product's own work is not reduced).  Count
+ * pass: row pointers of the result into rowptrP (int64[m+1], device) and its
+ * nnz to *nnz_host (waits); `ws` is spgemm_mask_workspace_size(m) bytes,
+ * 256-byte aligned.  Fill pass: colP (index type of C), valP (value type of
+ * C; NULL for BOOL); no wait.  Errors: INVALID_ARG, CUDA. */
+size_t spgemm_mask_workspace_size(int64_t m);
+spgemm_status spgemm_mask_count(const spgemm_csr* C, const spgemm_csr* M, int32_t complement,
+                                void* stream, void* ws, size_t ws_bytes, int64_t* rowptrP,
+                                int64_t* nnz_host);
+spgemm_status spgemm_mask_fill(const spgemm_csr* C, const spgemm_csr* M, int32_t complement,
+                               void* stream, const int64_t* rowptrP, void* colP, void* valP);
 spgemm_status spgemm_mcl_prune_count(const spgemm_csr* C, double threshold, void* stream,
                                      void* ws, size_t ws_bytes, int64_t* rowptrP,
                                      int64_t* nnz_host);

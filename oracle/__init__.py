@@ -23,9 +23,14 @@ Parts and the passages they follow:
                        paper; see ``oracle/mlp.py``).
 * ``mcl``           -- prune + column renormalisation of a Markov matrix
                        (Markov clustering expansion, Sec. 5.3).
+* ``spgemm`` semirings "min_plus" / "min_select2nd" and ``mask`` -- the
+                       operations MIS-2 aggregation is built from (Alg. 3):
+                       pinned by brute force, a path-graph closed form, the
+                       identity and a row-selection reduction; the mask by set
+                       identities (full mask, complement partition).
 """
 from .core import (OCSR, spgemm, sum_partials, kslice_bounds, kslice, transpose, row_flops,
-                   abs_bound, mcl_prune_renorm, lib_path, build, num_threads)
+                   abs_bound, mcl_prune_renorm, lib_path, build, num_threads, mask)
 
-__all__ = ["OCSR", "spgemm", "sum_partials", "kslice_bounds", "kslice", "transpose",
+__all__ = ["OCSR", "spgemm", "sum_partials", "kslice_bounds", "kslice", "transpose", "mask",
            "row_flops", "abs_bound", "mcl_prune_renorm", "lib_path", "build", "num_threads"]

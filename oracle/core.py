@@ -192,6 +192,23 @@ def sum_partials(parts: List, semiring: str = "plus_times", nthreads: int = 0) -
     return OCSR(m, n, rpC, ciC, vC)
 
 
+def mask(C, M, complement: bool = False) -> OCSR:
+    """Entries (i, j) of C with j in M(i,:) (or not in it, complement): the
+    structural mask MIS-2 applies to its products (Alg. 3), as a set filter
+    row by row."""
+    rpC, ciC = _idx(C.rowptr), _idx(C.col)
+    rpM, ciM = _idx(M.rowptr), _idx(M.col)
+    keep = np.zeros(ciC.size, dtype=bool)
+    for i in range(C.nrows):
+        a, b = rpC[i], rpC[i + 1]
+        keep[a:b] = np.isin(ciC[a:b], ciM[rpM[i]:rpM[i + 1]]) != complement
+    rows = np.repeat(np.arange(C.nrows), np.diff(rpC))[keep]
+    rp = np.zeros(C.nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=C.nrows), out=rp[1:])
+    val = None if C.val is None else np.asarray(C.val)[keep]
+    return OCSR(C.nrows, C.ncols, rp, ciC[keep], val)
+
+
 def kslice_bounds(l: int, c: int) -> List[tuple]:
     """K_s = [floor(s l / c), floor((s+1) l / c)), s = 0..c-1: contiguous,
     equal-size ranges of the inner dimension (the split distribution of

@@ -95,6 +95,9 @@ def _load():
         "spgemm_transpose_workspace_size": (S, [P]),
         "spgemm_sizer_param_count": (I32_, [I32_]),
         "spgemm_mcl_workspace_size": (S, [I64_]),
+        "spgemm_mask_workspace_size": (S, [I64_]),
+        "spgemm_mask_count": (st, [P, P, I32_, P, P, S, P, P]),
+        "spgemm_mask_fill": (st, [P, P, I32_, P, P, P, P]),
         "spgemm_mcl_prune_count": (st, [P, ctypes.c_double, P, P, S, P, P]),
         "spgemm_mcl_prune_fill": (st, [P, ctypes.c_double, P, P, S, P, P, P]),
         "spgemm_sizer_forward": (st, [P, I64_, I32_, P, P, P]),
@@ -427,6 +430,31 @@ def mcl_prune(C: DeviceCSR, threshold: float = 1e-4, stream=None) -> DeviceCSR:
                                       ctypes.c_void_p(col.data_ptr()) if nnz.value else None,
                                       ctypes.c_void_p(val.data_ptr()) if nnz.value else None))
     return DeviceCSR(C.nrows, C.ncols, rp, col, val)
+
+
+def mask(C: DeviceCSR, M: DeviceCSR, complement: bool = False, stream=None) -> DeviceCSR:
+    """Entries of C inside the pattern of M (or outside it with complement)."""
+    dev = C.rowptr.device
+    cC, cM = _csr(C), _csr(M)
+    ws = _workspace(_lib.spgemm_mask_workspace_size(C.nrows), dev)
+    rp = torch.empty(C.nrows + 1, dtype=torch.int64, device=dev)
+    nnz = ctypes.c_int64()
+    _check(_lib.spgemm_mask_count(ctypes.byref(cC), ctypes.byref(cM), 1 if complement else 0,
+                                  _stream(stream), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  ctypes.c_void_p(rp.data_ptr()), ctypes.byref(nnz)))
+    col = torch.empty(nnz.value, dtype=C.col.dtype, device=dev)
+    val = None if C.val is None else torch.empty(nnz.value, dtype=C.val.dtype, device=dev)
+    _check(_lib.spgemm_mask_fill(ctypes.byref(cC), ctypes.byref(cM), 1 if complement else 0,
+                                 _stream(stream), ctypes.c_void_p(rp.data_ptr()),
+                                 ctypes.c_void_p(col.data_ptr()) if col.numel() else None,
+                                 _ptr(val) if val is not None and val.numel() else None))
+    return DeviceCSR(C.nrows, C.ncols, rp, col, val)
+
+
+def masked_spgemm(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, semiring: int = PLUS_TIMES,
+                  complement: bool = False, stream=None) -> DeviceCSR:
+    """(A.B) restricted to the pattern of M (or to its complement)."""
+    return mask(spgemm(A, B, semiring, stream=stream), M, complement, stream)
 
 
 def mcl_step(M: DeviceCSR, threshold: float = 1e-4, params: Optional[torch.Tensor] = None,

@@ -82,3 +82,17 @@ def test_min_semiring_rejects_float32(sg):
     dA = sg.to_device(A)
     with pytest.raises(sg.SpgemmError):
         sg.spgemm(dA, dA, semiring=2)
+
+
+@pytest.mark.parametrize("complement", [False, True])
+@pytest.mark.parametrize("sr", [0, 2, 3])
+def test_masked_products(sg, complement, sr):
+    """(A.B) restricted to the pattern of M or to its complement, against the
+    oracle's set filter of the oracle's product."""
+    A = inputs.rmat(11, seed=90, value="int" if sr == 0 else "u01_f64")
+    M = inputs.random_csr(A.nrows, A.ncols, 0.02, 91, value="none", index_dtype=np.int32)
+    dA, dM = sg.to_device(A), sg.to_device(M)
+    C = sg.masked_spgemm(dA, dA, dM, semiring=sr, complement=complement)
+    name = {0: "plus_times", 2: "min_plus", 3: "min_select2nd"}[sr]
+    R = oracle.mask(oracle.spgemm(A, A, semiring=name), M, complement)
+    assert_equal_host(C, R)

@@ -383,3 +383,27 @@ def test_min_merge_of_kslices_equals_unsplit(sr, c):
     M = oracle.sum_partials(parts, semiring=sr)
     assert np.array_equal(M.rowptr, full.rowptr) and np.array_equal(M.col, full.col)
     assert np.array_equal(M.val, full.val)      # min keeps the first of equal terms
+
+
+# ------------------------------------------------------------ masks
+
+def test_mask_identities():
+    """A full mask keeps C, its complement keeps nothing; a mask and its
+    complement split C into two disjoint parts whose union is C; the masked
+    product equals the dense product times the 0/1 mask."""
+    A = inputs.random_csr(30, 25, 0.2, 11, value="u01_f64")
+    B = inputs.random_csr(25, 35, 0.2, 12, value="u01_f64")
+    C = oracle.spgemm(A, B)
+    full = oracle.mask(C, C)
+    assert np.array_equal(full.rowptr, C.rowptr) and np.array_equal(full.col, C.col)
+    assert np.array_equal(full.val, C.val)
+    assert oracle.mask(C, C, complement=True).col.size == 0
+    M = inputs.random_csr(30, 35, 0.3, 13, value="none")
+    In, Out = oracle.mask(C, M), oracle.mask(C, M, complement=True)
+    assert In.col.size + Out.col.size == C.col.size
+    assert not (pattern(In) & pattern(Out)).any()
+    assert np.array_equal(pattern(In) | pattern(Out), pattern(C))
+    assert np.array_equal(pattern(In), pattern(C) & pattern(M))
+    assert np.array_equal(dense(In), dense(C) * pattern(M))
+    assert_valid_csr(In)
+    assert_valid_csr(Out)
