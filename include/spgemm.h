@@ -319,6 +319,28 @@ size_t spgemm_mcl_workspace_size(int64_t m);
  * 256-byte aligned.  Fill pass: colP (index type of C), valP (value type of
  * C; NULL for BOOL); no wait.  Errors: INVALID_ARG, CUDA. */
 size_t spgemm_mask_workspace_size(int64_t m);
+
+/* ---- MIS-2 aggregation: the restriction operator of the paper's AMG
+ *      experiments (Sec. 5.4, Alg. 3) ----
+ * A: square CSR (the graph; its pattern only is read, diagonal allowed; rows
+ * sorted; at most 2^31-1 vertices).  Computes a distance-2 maximal
+ * independent set with Alg. 3's rounds of (min, select2nd) products: a
+ * candidate joins when its key is the smallest within distance 2, where
+ * key(seed, t, v) = ((splitmix64(seed ^ (t * 0xD1B54A32D192ED03) + v) >> 33)
+ * << 31) | v in round t (SplitMix64 as published); the new members and every
+ * candidate within distance 2 of them leave the candidates.  Aggregates:
+ * members in increasing vertex order own themselves and their neighbours;
+ * every other vertex joins the smallest-numbered aggregate among its
+ * neighbours.  Writes R (n x naggs, one 1.0 per row): rowptrR int64[n+1],
+ * colR (index type of A) [n], valR double[n]; *naggs_host, *rounds_host.
+ * Waits for the stream once per round.  `ws` is
+ * spgemm_mis2_workspace_size(n) bytes, 256-byte aligned.  Errors:
+ * INVALID_ARG, NOT_SUPPORTED, INTERNAL (no progress / unaggregated vertex,
+ * which the construction rules out), CUDA. */
+size_t spgemm_mis2_workspace_size(int64_t n);
+spgemm_status spgemm_mis2_restriction(const spgemm_csr* A, uint64_t seed, void* stream, void* ws,
+                                      size_t ws_bytes, int64_t* rowptrR, void* colR,
+                                      double* valR, int64_t* naggs_host, int32_t* rounds_host);
 spgemm_status spgemm_mask_count(const spgemm_csr* C, const spgemm_csr* M, int32_t complement,
                                 void* stream, void* ws, size_t ws_bytes, int64_t* rowptrP,
                                 int64_t* nnz_host);

@@ -96,6 +96,8 @@ def _load():
         "spgemm_sizer_param_count": (I32_, [I32_]),
         "spgemm_mcl_workspace_size": (S, [I64_]),
         "spgemm_mask_workspace_size": (S, [I64_]),
+        "spgemm_mis2_workspace_size": (S, [I64_]),
+        "spgemm_mis2_restriction": (st, [P, ctypes.c_uint64, P, P, S, P, P, P, P, P]),
         "spgemm_mask_count": (st, [P, P, I32_, P, P, S, P, P]),
         "spgemm_mask_fill": (st, [P, P, I32_, P, P, P, P]),
         "spgemm_mcl_prune_count": (st, [P, ctypes.c_double, P, P, S, P, P]),
@@ -449,6 +451,26 @@ def mask(C: DeviceCSR, M: DeviceCSR, complement: bool = False, stream=None) -> D
                                  ctypes.c_void_p(col.data_ptr()) if col.numel() else None,
                                  _ptr(val) if val is not None and val.numel() else None))
     return DeviceCSR(C.nrows, C.ncols, rp, col, val)
+
+
+def mis2_restriction(A: DeviceCSR, seed: int, stream=None):
+    """MIS-2 aggregation of the graph of A (spgemm_mis2_restriction): returns
+    (R as a DeviceCSR n x naggs with values 1.0, rounds)."""
+    dev = A.rowptr.device
+    n = A.nrows
+    ws = _workspace(_lib.spgemm_mis2_workspace_size(n), dev)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(n, 1), dtype=A.col.dtype, device=dev)
+    val = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    naggs = ctypes.c_int64()
+    rounds = ctypes.c_int32()
+    _check(_lib.spgemm_mis2_restriction(ctypes.byref(_csr(A)), ctypes.c_uint64(seed),
+                                        _stream(stream), ctypes.c_void_p(ws.data_ptr()),
+                                        ws.numel(), ctypes.c_void_p(rp.data_ptr()),
+                                        ctypes.c_void_p(col.data_ptr()),
+                                        ctypes.c_void_p(val.data_ptr()), ctypes.byref(naggs),
+                                        ctypes.byref(rounds)))
+    return DeviceCSR(n, int(naggs.value), rp, col[:n], val[:n]), int(rounds.value)
 
 
 def masked_spgemm(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, semiring: int = PLUS_TIMES,
