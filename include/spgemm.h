@@ -23,11 +23,13 @@
  *   0-based indices; C is produced the same way (the paper keeps columns
  *   sorted, Sec. 5.2).  The pattern is structural: products that sum to zero
  *   stay in C (explicit zeros are nonzeros, Sec. 5).
- * - Values: F64, F32 and I64 use the (+, x) semiring (I64 wraps around);
- *   BOOL is the (or, and) semiring and carries no value array.  Every output
- *   entry is the sum of its products in ascending k, each product rounded
- *   before it is added (no fused multiply-add), so F64/F32 results are
- *   reproducible bit for bit from run to run.
+ * - Values: F64, F32 and I64 use the (+, x) semiring by default (I64 wraps
+ *   around); BOOL is the (or, and) semiring and carries no value array; the
+ *   (min, +) and (min, select2nd) semirings run on F64 and I64 values (see
+ *   spgemm_semiring).  Every output entry reduces its products in ascending
+ *   k, each product rounded before it is added (no fused multiply-add), so
+ *   results are reproducible bit for bit from run to run and equal across
+ *   the single, batched, device-sized and learned paths.
  * - Work is enqueued on the caller's CUDA stream (a cudaStream_t passed as
  *   void*; NULL = legacy default stream).  The calls that report a size to
  *   the host (spgemm_plan, spgemm_symbolic, spgemm_merge_symbolic) wait for
