@@ -301,9 +301,32 @@ def run_paths(args, A, dA, sg, torch):
     tb = _timed(torch, lambda: sg.batch_spgemm(As, Bs), reps)
     ts = _timed(torch, lambda: [sg.spgemm(a, b) for a, b in zip(As, Bs)], reps)
     best, table = autotune.batch(As, Bs, repeats=2)
+    # the same batch as one device-sized plan captured in a CUDA graph (no
+    # host readback; output capacity = the flops bound)
+    gs = torch.cuda.Stream()
+    dp = sg.device_plan(As, Bs, stream=gs, max_row_nnz=4096)
+    rowptrC = torch.empty(dp.R + 1, dtype=torch.int64, device="cuda")
+    colC = torch.empty(int(bflops), dtype=As[0].col.dtype, device="cuda")
+    valC = torch.empty(int(bflops), dtype=As[0].val.dtype, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        sg.execute(dp, rowptrC, int(bflops), colC, valC)
+    graph.replay()
+    torch.cuda.synchronize()
+    sg.check(dp)
+    tgb = _timed(torch, graph.replay, reps)
+    ref = sg.batch_spgemm(As, Bs)
+    nnz = int(rowptrC[-1].item())
+    same = (nnz == sum(C.nnz for C in ref)
+            and bool((colC[:nnz] == torch.cat([C.col for C in ref])).all())
+            and bool((valC[:nnz] == torch.cat([C.val for C in ref])).all()))
+    del ref, graph, dp, rowptrC, colC, valC
     out["batched_er512_f32"] = {"batched_ms": round(tb * 1e3, 3), "sequential_ms": round(ts * 1e3, 3),
                                 "speedup": round(ts / tb, 3), "flops": int(bflops),
                                 "gflops_batched": round(2 * bflops / tb / 1e9, 3),
+                                "graph_ms": round(tgb * 1e3, 3),
+                                "graph_speedup_vs_sequential": round(ts / tgb, 3),
+                                "graph_bit_identical": bool(same),
                                 "autotune": _tuning_report(best, table)}
     del As, Bs, pairs
     N = 128

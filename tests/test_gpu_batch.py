@@ -191,3 +191,28 @@ def test_product_to_host_in_panels(sg, panels, semiring):
         assert np.array_equal(H.val[:H.nnz].numpy(), C.val.cpu().numpy())
     H2 = pipeline.spgemm_to_host(dA, dA, semiring=semiring, panels=panels + 1, out=H)
     assert H2 is H and np.array_equal(H2.col[:H2.nnz].numpy(), C.col.cpu().numpy())
+
+
+def test_batch_captured_in_a_graph(sg):
+    """A batch of uneven products as one device-sized plan captured in a CUDA
+    graph: replays give the host-synced batch's result bit for bit."""
+    import torch
+    pairs = inputs.batched_er(24, nmin=256, nmax=4096)
+    As = [sg.to_device(a) for a, _ in pairs]
+    Bs = [sg.to_device(b) for _, b in pairs]
+    cap = int(sg.batch_plan(As, Bs).info()["flops"])
+    s = torch.cuda.Stream()
+    p = sg.device_plan(As, Bs, stream=s, max_row_nnz=4096)
+    rowptrC = torch.empty(p.R + 1, dtype=torch.int64, device="cuda")
+    colC = torch.empty(cap, dtype=As[0].col.dtype, device="cuda")
+    valC = torch.empty(cap, dtype=As[0].val.dtype, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sg.execute(p, rowptrC, cap, colC, valC)
+    ref = sg.batch_spgemm(As, Bs)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        sg.check(p)
+        for C, R in zip(sg.split_batch(p, rowptrC, colC, valC), ref):
+            assert bool((C.col == R.col).all()) and bool((C.val == R.val).all())
