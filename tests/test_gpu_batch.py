@@ -130,7 +130,7 @@ def test_device_sized_capacity_overflow_is_reported(sg):
     assert int(rowptrC[-1].item()) == oracle.spgemm(M, M).nnz
 
 
-@pytest.mark.parametrize("N,levels", [(16, 2), (32, 3)])
+@pytest.mark.parametrize("N,levels", [(16, 2), (32, 3), (128, 3)])
 def test_amg_hierarchy_in_one_graph(sg, N, levels):
     import torch
     from paper_1510_00844_gb300 import amg
@@ -216,3 +216,22 @@ def test_batch_captured_in_a_graph(sg):
         sg.check(p)
         for C, R in zip(sg.split_batch(p, rowptrC, colC, valC), ref):
             assert bool((C.col == R.col).all()) and bool((C.val == R.val).all())
+
+
+def test_full_batch_of_512_products_sampled(sg):
+    """The full batched workload (512 uneven ER products, f32) with one plan;
+    a seeded sample of products, always including the largest, is checked
+    against the oracle (pattern exact, values within the f32 summation
+    bound)."""
+    pairs = inputs.batched_er(512)
+    As = [sg.to_device(a) for a, _ in pairs]
+    Bs = [sg.to_device(b) for _, b in pairs]
+    Cs = sg.batch_spgemm(As, Bs, verify=True)
+    sizes = np.array([a.nrows for a, _ in pairs])
+    rng = np.random.default_rng(11)
+    pick = np.unique(np.concatenate([np.argsort(-sizes)[:2], rng.choice(512, 10, replace=False)]))
+    for q in pick:
+        a, b = pairs[q]
+        R = oracle.spgemm(a, b)
+        assert_pattern_equal(Cs[q], R)
+        assert_values_close(Cs[q], R, a, b, dtype="f32")

@@ -146,3 +146,31 @@ def test_learned_rerun_rows_go_to_spare_space(sg, trained):
     Cc = sg.compact(C)
     assert bool((Cc.rowptr == P.rowptr).all())
     assert bool((Cc.col == P.col).all()) and bool((Cc.val == P.val).all())
+
+
+def test_rmat_scale20_panel_sampled_rows(sg):
+    """The learned-sizing workload at full size: R-MAT scale 20 squaring on one
+    row panel (1/16 of the rows, as the benchmark runs it) by the exact
+    two-phase path and by learned sizing; the two agree bit for bit and a
+    seeded sample of rows, including the panel's largest, matches the oracle
+    row by row."""
+    from tests.parity import rows_subset
+    params = train_small(sg)[0]
+    A = inputs.rmat(20)
+    dA = sg.to_device(A)
+    a, b = 0, A.nrows // 16
+    view = sg.DeviceCSR(b - a, A.ncols, dA.rowptr[a:b], dA.col, dA.val, rowend=dA.rowptr[a + 1:b + 1])
+    C = sg.spgemm(view, dA, verify=True)
+    L, _ = sg.learned_multiply(view, dA, params, margin=0.35)
+    Lc = sg.compact(L)
+    assert bool((Lc.rowptr == C.rowptr).all()) and bool((Lc.col == C.col).all())
+    assert bool((Lc.val == C.val).all())
+    fl = oracle.row_flops(rows_subset(A, np.arange(a, b)), A)
+    rng = np.random.default_rng(13)
+    rows = np.unique(np.concatenate([np.argsort(-fl)[:4], rng.choice(b - a, 200, replace=False)]))
+    R = oracle.spgemm(rows_subset(A, rows + a), A)
+    rp, col, val = C.rowptr.cpu().numpy(), C.col.cpu().numpy(), C.val.cpu().numpy()
+    for t, i in enumerate(rows):
+        x, y = rp[i], rp[i + 1]
+        u, v = R.rowptr[t], R.rowptr[t + 1]
+        assert np.array_equal(col[x:y], R.col[u:v]) and np.array_equal(val[x:y], R.val[u:v])
