@@ -115,16 +115,25 @@ def algorithmic_bytes(A, nnz_c: int):
     return sym, num
 
 
+def dense_kernel_digest():
+    """sha256 (first 16 hex) of the numeric_dense_kernel source: from its
+    section comment to the next section comment of kernels.cuh."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1510_00844_gb300", "csrc", "kernels.cuh")
+    text = open(src).read()
+    a = text.index("// --------------------------------------------------- numeric: dense rows")
+    b = text.index("// ------------------------------------------------------------ k-slices", a)
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per launch of numeric_dense_kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "numeric_dense_rmat18.md")
-    src = os.path.join(ROOT, "paper_1510_00844_gb300", "csrc", "kernels.cuh")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+        digest = dense_kernel_digest()
+    except (OSError, ValueError):
         return None
     if f"`{digest}`" not in text:
         return None

@@ -614,18 +614,36 @@ __global__ void __launch_bounds__(WARPS * 32)
                 len = (int)(rpB[k + 1] - lo);
                 a = load_val(vA, b + lane);
             }
-            walk_batch(nb, lo, len, [&](long long q, int e, bool valid, bool ordered) {
-                V ae = shfl_val(a, e);
-                int slot = -1;
-                V v{};
-                if (valid) {
-                    bool is_new;
-                    slot = hash_insert<LOG2T>(keys, (K)ciB[q], is_new, fail);
-                    v = VOps<V>::mul(ae, load_val(vB, q));
+            // four rounds per step: their loads are issued together, then
+            // the rounds are inserted and accumulated in order
+            walk_batch4(nb, lo, len, [&](const long long (&q)[4], const int (&e)[4],
+                                         const bool (&vl)[4], bool ordered) {
+                K key[4];
+                V bq[4];
+                V ae[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    ae[t] = shfl_val(a, e[t]);
+                    key[t] = K(-1);
+                    bq[t] = V{};
+                    if (vl[t]) {
+                        key[t] = (K)ciB[q[t]];
+                        bq[t] = load_val(vB, q[t]);
+                    }
                 }
-                valid = valid && slot >= 0;
-                if (ordered) ordered_add(acc, slot, valid, v);
-                else plain_add(acc, slot, valid, v);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    int slot = -1;
+                    V v{};
+                    if (vl[t]) {
+                        bool is_new;
+                        slot = hash_insert<LOG2T>(keys, key[t], is_new, fail);
+                        v = VOps<V>::mul(ae[t], bq[t]);
+                    }
+                    const bool valid = vl[t] && slot >= 0;
+                    if (ordered) ordered_add(acc, slot, valid, v);
+                    else plain_add(acc, slot, valid, v);
+                }
             });
         }
         // compact occupied slots to the front (ascending slot order)
