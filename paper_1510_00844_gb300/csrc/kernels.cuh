@@ -1,18 +1,20 @@
 // Kernels of the two-phase sparse product C = A.B (Gustavson, Alg. 1, on
-// CSR rows) and of the k-slice merge (Sec. 4.3).  Templates over the column
+// CSR rows) and the k-slice bounds (Sec. 4.1).  Templates over the column
 // index type IT (int32_t / int64_t) and the value type V (double, float,
-// int64_t, NoVal for the Boolean semiring).
+// int64_t, the min-semiring wrappers, NoVal for the Boolean semiring).
 //
 // Row classes (decided from flops_i = sum_{k in A(i,:)} nnz(B(k,:)), Sec. 2):
 //   EMPTY       flops_i == 0
-//   HASH(b)     flops_i <= 1024: one warp per row, warp-private hash table in
-//               shared memory (keys for the symbolic phase, keys + values for
-//               the numeric phase), output sorted by a warp bitonic sort.
-//   DENSE(b)    flops_i > 1024: symbolic = one block per row with a bitmap of
-//               all n columns in shared memory (also yields per-chunk counts);
-//               numeric = one warp per row sweeping column chunks of width W
-//               with a dense accumulator, so the output comes out sorted.
-//               DENSE rows are bucketed by floor(log2 flops_i), largest first.
+//   HASH(b)     flops_i <= dense_min (<= 1024): one warp per row, warp-private
+//               hash table in shared memory (keys for the symbolic phase, keys
+//               + values for the numeric phase), output sorted in the warp
+//               (bitonic sort up to 64 entries, stable radix sort above).
+//   DENSE(b)    flops_i > dense_min: symbolic = one block per row with a
+//               bitmap of all n columns in shared memory (also yields
+//               per-chunk counts); numeric = one warp per (row, column
+//               segment) sweeping column chunks of width W with a dense
+//               accumulator, so the output comes out sorted.  DENSE rows are
+//               bucketed by floor(log2 flops_i), largest first.
 #pragma once
 
 #include "device_common.cuh"
