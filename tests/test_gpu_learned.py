@@ -174,3 +174,20 @@ def test_rmat_scale20_panel_sampled_rows(sg):
         x, y = rp[i], rp[i + 1]
         u, v = R.rowptr[t], R.rowptr[t + 1]
         assert np.array_equal(col[x:y], R.col[u:v]) and np.array_equal(val[x:y], R.val[u:v])
+
+
+def test_learned_with_a_broken_predictor_stays_exact(sg):
+    """NaN parameters make every prediction NaN: capacities clamp to the
+    exact lower bound max_k |B(k,:)| and rows that need more are re-run, so C
+    still equals the two-phase product bit for bit (int64 indices here)."""
+    import torch
+    A = inputs.rmat(12, seed=97, index_dtype=np.int64)
+    dA = sg.to_device(A)
+    params = torch.full((sg.sizer_param_count(),), float("nan"), dtype=torch.float32,
+                        device="cuda")
+    C, stats = sg.learned_multiply(dA, dA, params, margin=0.3)
+    P = sg.spgemm(dA, dA)
+    Cc = sg.compact(C)
+    assert stats["overflow_rows"] > 0
+    assert bool((Cc.rowptr == P.rowptr).all()) and bool((Cc.col == P.col).all())
+    assert bool((Cc.val == P.val).all())
