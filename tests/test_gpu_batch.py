@@ -235,3 +235,26 @@ def test_full_batch_of_512_products_sampled(sg):
         R = oracle.spgemm(a, b)
         assert_pattern_equal(Cs[q], R)
         assert_values_close(Cs[q], R, a, b, dtype="f32")
+
+
+def test_split3d_on_one_rank(sg, tmp_path):
+    """Alg. 2 with the library's kernels on a 1 x 1 x 1 grid: the broadcasts
+    and all-to-alls reach only this rank; the result is the product."""
+    import torch
+    import torch.distributed as dist
+    from paper_1510_00844_gb300 import split3d as s3
+    store = dist.FileStore(str(tmp_path / "store3d"), 1)
+    dist.init_process_group("gloo", store=store, rank=0, world_size=1)
+    try:
+        A = inputs.rmat(10, seed=63)
+        dA = sg.to_device(A)
+        P = (A.nrows, A.ncols, dA.rowptr, dA.col, dA.val)
+        multiply, merge = s3.gpu_ops()
+        grid = s3.Grid(1, 1)
+        m, n, rp, col, val = s3.split3d(grid, P, P, (A.nrows, A.ncols, A.ncols), multiply, merge,
+                                        dA.col.dtype, dA.val.dtype, torch.device("cuda"))
+        C = sg.spgemm(dA, dA)
+        assert bool((rp == C.rowptr).all()) and bool((col == C.col).all())
+        assert bool((val == C.val).all())
+    finally:
+        dist.destroy_process_group()

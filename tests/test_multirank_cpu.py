@@ -125,3 +125,76 @@ def test_kslice_exchange_over_gloo(tmp_path, world):
     mp.start_processes(_kslice_worker, args=(world, _free_port(), str(out)), nprocs=world,
                        start_method="spawn", join=True)
     assert out.read_text() == "ok"
+
+
+def _split3d_worker(rank, world, port, q, c, out_path):
+    import torch
+    import oracle
+    from paper_1510_00844_gb300 import inputs, split3d as s3
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    A = inputs.random_csr(90, 70, 0.06, 21, value="int", index_dtype=np.int64)
+    B = inputs.random_csr(70, 110, 0.06, 22, value="int", index_dtype=np.int64)
+    m, l, n = A.nrows, A.ncols, B.ncols
+
+    def piece(M):
+        return (M.nrows, M.ncols, torch.from_numpy(np.asarray(M.rowptr, dtype=np.int64)),
+                torch.from_numpy(np.asarray(M.col, dtype=np.int64)),
+                torch.from_numpy(np.asarray(M.val, dtype=np.int64)))
+
+    def owned(M, rows_parts, i, j, k):
+        r0, r1 = s3.block(M.nrows, q, i)
+        c0, c1 = s3.sub(M.ncols, q, c, j, k)
+        return s3.cols_range(s3.rows_range(piece(M), r0, r1), c0, c1)
+
+    def to_csr(P):
+        m_, n_, rp, col, val = P
+        return inputs.CSR(m_, n_, rp.numpy(), col.numpy(), val.numpy())
+
+    def multiply(a, b):                       # the local multiply (HeapSpGEMM's role)
+        C = oracle.spgemm(to_csr(a), to_csr(b))
+        return piece(C)
+
+    def merge(ps):                            # LocalMerge
+        return piece(oracle.sum_partials([to_csr(P) for P in ps]))
+
+    grid = s3.Grid(q, c)
+    i, j, k = grid.i, grid.j, grid.k
+    Cp = s3.split3d(grid, owned(A, q, i, j, k), owned(B, q, i, j, k), (m, l, n), multiply, merge,
+                    torch.int64, torch.int64, torch.device("cpu"))
+    parts = [None] * world
+    dist.all_gather_object(parts, (i, j, k, Cp[2].numpy(), Cp[3].numpy(), Cp[4].numpy()))
+    if rank == 0:
+        full = oracle.spgemm(A, B)
+        D = np.zeros((m, n), dtype=np.int64)
+        P = np.zeros((m, n), dtype=bool)
+        for (pi, pj, pk, rp, col, val) in parts:
+            r0, _ = s3.block(m, q, pi)
+            c0, _ = s3.sub(n, q, c, pj, pk)
+            rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp)) + r0
+            D[rows, col + c0] = val
+            P[rows, col + c0] = True
+        rows = np.repeat(np.arange(m), np.diff(full.rowptr))
+        D2 = np.zeros((m, n), dtype=np.int64)
+        P2 = np.zeros((m, n), dtype=bool)
+        D2[rows, full.col] = full.val
+        P2[rows, full.col] = True
+        ok = np.array_equal(P, P2) and np.array_equal(D, D2)
+        with open(out_path, "w") as fh:
+            fh.write("ok" if ok else "mismatch")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("q,c", [(2, 1), (2, 2), (1, 3)])
+def test_split3d_over_gloo(tmp_path, q, c):
+    """Alg. 2 on a q x q x c grid of CPU ranks: B's all-to-all across layers,
+    the SUMMA broadcasts of A and B^, the local multiplies, C^int's
+    all-to-all and the local merge give exactly the product (integer values,
+    so any summation order is exact)."""
+    out = tmp_path / "result.txt"
+    world = q * q * c
+    mp.start_processes(_split3d_worker, args=(world, _free_port(), q, c, str(out)), nprocs=world,
+                       start_method="spawn", join=True)
+    assert out.read_text() == "ok"
