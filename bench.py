@@ -299,9 +299,13 @@ def run_paths(args, A, dA, sg, torch):
     flops = sg.plan(dA, dA).info()["flops"]
     _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4), 1)
     t = _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4), reps)
+    _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4, hypersparse=True), 1)
+    th = _timed(torch, lambda: sg.spgemm_kslice(dA, dA, 4, hypersparse=True), reps)
     out["kslice4_merge_rmat18"] = {"ms": round(t * 1e3, 3),
                                    "gflops": round(2 * flops / t / 1e9, 3),
-                                   "note": "4 k-slice partial products + multiway merge"}
+                                   "hypersparse_slices_ms": round(th * 1e3, 3),
+                                   "note": "4 k-slice partial products + multiway merge; "
+                                           "hypersparse: slices as DCSR views"}
     pairs = inputs.batched_er(512)
     As = [sg.to_device(a) for a, _ in pairs]
     Bs = [sg.to_device(b) for _, b in pairs]

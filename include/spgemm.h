@@ -340,6 +340,24 @@ size_t spgemm_mask_workspace_size(int64_t m);
  * INVALID_ARG, NOT_SUPPORTED, INTERNAL (no progress / unaggregated vertex,
  * which the construction rules out), CUDA. */
 size_t spgemm_mis2_workspace_size(int64_t n);
+
+/* ---- doubly compressed rows (the row-wise form of DCSC, Sec. 3: only rows
+ *      with entries are represented, with their ids) ----
+ * spgemm_dcsr_view lists the nonempty rows of A (a CSR or a view, e.g. a
+ * k-slice): rowids[t], rowptr_v[t], rowend_v[t] for t < *nzr_host (device
+ * arrays of at least A->nrows entries; ids ascending).  {nrows = nzr, rowptr =
+ * rowptr_v, rowend = rowend_v, col/val of A} is a view of those rows, and the
+ * product of that view has the same column and value arrays as the product
+ * of A; spgemm_dcsr_expand turns its row pointers (rowptr_c, nzr+1 entries)
+ * back into the m+1 row pointers of the full product (rowptr_full).  `ws` is
+ * spgemm_dcsr_workspace_size(m) bytes, 256-byte aligned.  The view call
+ * waits for the stream (it reads nzr back); expand does not. */
+size_t spgemm_dcsr_workspace_size(int64_t m);
+spgemm_status spgemm_dcsr_view(const spgemm_csr* A, void* stream, void* ws, size_t ws_bytes,
+                               int64_t* rowids, int64_t* rowptr_v, int64_t* rowend_v,
+                               int64_t* nzr_host);
+spgemm_status spgemm_dcsr_expand(int64_t m, int64_t nzr, const int64_t* rowids,
+                                 const int64_t* rowptr_c, void* stream, int64_t* rowptr_full);
 spgemm_status spgemm_mis2_restriction(const spgemm_csr* A, uint64_t seed, void* stream, void* ws,
                                       size_t ws_bytes, int64_t* rowptrR, void* colR,
                                       double* valR, int64_t* naggs_host, int32_t* rounds_host);

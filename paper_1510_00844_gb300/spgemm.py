@@ -97,6 +97,9 @@ def _load():
         "spgemm_mcl_workspace_size": (S, [I64_]),
         "spgemm_mask_workspace_size": (S, [I64_]),
         "spgemm_mis2_workspace_size": (S, [I64_]),
+        "spgemm_dcsr_workspace_size": (S, [I64_]),
+        "spgemm_dcsr_view": (st, [P, P, P, S, P, P, P, P]),
+        "spgemm_dcsr_expand": (st, [I64_, I64_, P, P, P, P]),
         "spgemm_mis2_restriction": (st, [P, ctypes.c_uint64, P, P, S, P, P, P, P, P]),
         "spgemm_mask_count": (st, [P, P, I32_, P, P, S, P, P]),
         "spgemm_mask_fill": (st, [P, P, I32_, P, P, P, P]),
@@ -453,6 +456,32 @@ def mask(C: DeviceCSR, M: DeviceCSR, complement: bool = False, stream=None) -> D
     return DeviceCSR(C.nrows, C.ncols, rp, col, val)
 
 
+def dcsr_view(A: DeviceCSR, stream=None):
+    """The nonempty rows of A (spgemm_dcsr_view): returns (rowids, view)."""
+    dev = A.rowptr.device
+    m = A.nrows
+    ws = _workspace(_lib.spgemm_dcsr_workspace_size(m), dev)
+    ids = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+    rp = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+    re = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+    nzr = ctypes.c_int64()
+    _check(_lib.spgemm_dcsr_view(ctypes.byref(_csr(A)), _stream(stream),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                 ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(rp.data_ptr()),
+                                 ctypes.c_void_p(re.data_ptr()), ctypes.byref(nzr)))
+    k = int(nzr.value)
+    return ids[:k], DeviceCSR(k, A.ncols, rp[:k], A.col, A.val, rowend=re[:k])
+
+
+def dcsr_expand(C: DeviceCSR, rowids: torch.Tensor, m: int, stream=None) -> DeviceCSR:
+    """The product of a DCSR view with its row pointers expanded to all m rows."""
+    full = torch.empty(m + 1, dtype=torch.int64, device=C.rowptr.device)
+    _check(_lib.spgemm_dcsr_expand(m, C.nrows, ctypes.c_void_p(rowids.data_ptr()) if C.nrows else None,
+                                   ctypes.c_void_p(C.rowptr.data_ptr()), _stream(stream),
+                                   ctypes.c_void_p(full.data_ptr())))
+    return DeviceCSR(m, C.ncols, full, C.col, C.val)
+
+
 def mis2_restriction(A: DeviceCSR, seed: int, stream=None):
     """MIS-2 aggregation of the graph of A (spgemm_mis2_restriction): returns
     (R as a DeviceCSR n x naggs with values 1.0, rounds)."""
@@ -728,10 +757,17 @@ def merge(parts: Sequence[DeviceCSR], semiring: int = PLUS_TIMES, stream=None,
 
 
 def spgemm_kslice(A: DeviceCSR, B: DeviceCSR, c: int, semiring: int = PLUS_TIMES,
-                  stream=None, verify: bool = False):
+                  stream=None, verify: bool = False, hypersparse: bool = False):
     """The k-split product: C_s = A(:,K_s).B for the c contiguous slices K_s
-    of the inner dimension, then C = sum_s C_s by the merge.  Returns
-    (C, partials)."""
-    parts = [spgemm(As, B, semiring, stream=stream, verify=verify)
-             for As in kslice_views(A, c, stream)]
+    of the inner dimension, then C = sum_s C_s by the merge.  With
+    hypersparse, each slice is multiplied as a DCSR view of its nonempty rows
+    and its row pointers are expanded afterwards.  Returns (C, partials)."""
+    parts = []
+    for As in kslice_views(A, c, stream):
+        if hypersparse:
+            ids, v = dcsr_view(As, stream)
+            Cv = spgemm(v, B, semiring, stream=stream, verify=verify)
+            parts.append(dcsr_expand(Cv, ids, A.nrows, stream))
+        else:
+            parts.append(spgemm(As, B, semiring, stream=stream, verify=verify))
     return merge(parts, semiring, stream, verify), parts

@@ -252,3 +252,27 @@ def test_rmat_scale18_sampled_rows(sg):
     # global invariants at full size
     assert int(rp[-1]) <= int(fl.sum())
     assert np.all(np.diff(rp) <= np.minimum(fl, A.ncols))
+
+
+@pytest.mark.parametrize("c", [1, 4, 16])
+def test_hypersparse_kslices(sg, c):
+    """k-slices multiplied as DCSR views of their nonempty rows (many rows of
+    a slice are empty) give the same partials and the same merged product as
+    the plain slices; row panels too."""
+    A = inputs.rmat(12, seed=101)
+    dA = sg.to_device(A)
+    C1, P1 = sg.spgemm_kslice(dA, dA, c)
+    C2, P2 = sg.spgemm_kslice(dA, dA, c, hypersparse=True)
+    for a, b in zip(P1, P2):
+        assert bool((a.rowptr == b.rowptr).all()) and bool((a.col == b.col).all())
+        assert bool((a.val == b.val).all())
+    assert bool((C1.rowptr == C2.rowptr).all()) and bool((C1.col == C2.col).all())
+    assert bool((C1.val == C2.val).all())
+    ids, v = sg.dcsr_view(dA)
+    empty = np.diff(A.rowptr) == 0
+    assert v.nrows == int((~empty).sum())
+    assert np.array_equal(ids.cpu().numpy(), np.flatnonzero(~empty))
+    R = oracle.spgemm(A, A)
+    E = sg.dcsr_expand(sg.spgemm(v, dA), ids, A.nrows)
+    assert_pattern_equal(E, R)
+    assert np.array_equal(E.to_host()[2], R.val)
