@@ -30,9 +30,10 @@ def assert_equal_host(C, R):
 
 @pytest.mark.parametrize("sr", [2, 3])
 @pytest.mark.parametrize("value", ["u01_f64", "int"])
-@pytest.mark.parametrize("gen", ["rmat12", "er"])
+@pytest.mark.parametrize("gen", ["rmat12", "er", "rmat12_i64"])
 def test_min_semiring_products(sg, sr, value, gen):
     A = (inputs.rmat(12, seed=81, value=value) if gen == "rmat12"
+         else inputs.rmat(12, seed=81, value=value, index_dtype=np.int64) if gen == "rmat12_i64"
          else inputs.er_column_regular(4096, 12, 82, value=value))
     dA = sg.to_device(A)
     C = sg.spgemm(dA, dA, semiring=sr, verify=True)
