@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // per-chunk counts chunkcnt[chunk_base + i*P + c] (chunk c covers columns
 // [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
 template <class IT>
-__global__ void __launch_bounds__(512, 3) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+__global__ void __launch_bounds__(256, 6) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
                                       const long long* __restrict__ rb, int nprod,
                                       const int32_t* __restrict__ rows, const DevCounters* cnt,
                                       int max_words, int chunk_words,

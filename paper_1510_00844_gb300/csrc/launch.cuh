@@ -143,7 +143,7 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
     if ((e = launch_dense_tables<IT>(P, ws)) != cudaSuccess) return e;
     if (dense) {
         auto k = symbolic_dense_kernel<IT>;
-        const int threads = 512;
+        const int threads = 256;
         const int max_words = (int)((std::min(P.max_n, P.max_dense_n) + 31) / 32);
         size_t smem = (size_t)max_words * 4;
         if ((e = allow_smem(k, smem)) != cudaSuccess) return e;
