@@ -391,8 +391,11 @@ __global__ void __launch_bounds__(WARPS * 32)
 // in shared memory (sized for the largest n of the batch).  Also writes the
 // per-chunk counts chunkcnt[chunk_base + i*P + c] (chunk c covers columns
 // [c*W, (c+1)*W)), which the numeric phase uses to skip empty chunks.
-template <class IT>
-__global__ void __launch_bounds__(256, 6) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+// MAXT / MINB: launch bounds of the instantiation (a register cap that lets
+// six 256-thread or three 512-thread blocks share an SM, or one 1024-thread
+// block for a bitmap that leaves room for only one block).
+template <class IT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
                                       const long long* __restrict__ rb, int nprod,
                                       const int32_t* __restrict__ rows, const DevCounters* cnt,
                                       int max_words, int chunk_words,

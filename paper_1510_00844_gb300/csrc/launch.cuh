@@ -142,21 +142,35 @@ cudaError_t launch_symbolic(Plan& P, unsigned char* ws, int64_t* rowcnt) {
     const bool dense = P.device_sized || P.ndense > 0;
     if ((e = launch_dense_tables<IT>(P, ws)) != cudaSuccess) return e;
     if (dense) {
-        auto k = symbolic_dense_kernel<IT>;
-        const int threads = 256;
+        // one block per row; the block size follows the bitmap: the most
+        // resident warps, and among equals the smaller blocks (more rows in
+        // flight) -- 256 threads while six blocks fit, 1024 when only one does
+        auto ks = symbolic_dense_kernel<IT, 512, 3>;
+        auto kb = symbolic_dense_kernel<IT, 1024, 1>;
         const int max_words = (int)((std::min(P.max_n, P.max_dense_n) + 31) / 32);
         size_t smem = (size_t)max_words * 4;
-        if ((e = allow_smem(k, smem)) != cudaSuccess) return e;
-        int occ = occupancy_blocks(k, threads, smem);
+        if ((e = allow_smem(ks, smem)) != cudaSuccess) return e;
+        if ((e = allow_smem(kb, smem)) != cudaSuccess) return e;
+        int threads = 256, occ = occupancy_blocks(ks, 256, smem);
+        const int o512 = occupancy_blocks(ks, 512, smem);
+        if (o512 * 512 > occ * threads) { threads = 512; occ = o512; }
+        const int o1024 = occupancy_blocks(kb, 1024, smem);
+        if (o1024 * 1024 > occ * threads) { threads = 1024; occ = o1024; }
         long long g = class_grid(P, P.ndense, 1, occ);
         unsigned long long* work = &P.cnt->work_counter[0];
         if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), P.stream)) != cudaSuccess)
             return e;
         count_launches(1);
-        k<<<(unsigned)g, threads, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt,
-                                                    max_words, P.W / 32,
-                                                    (int32_t*)(ws + L.chunkcnt), rowcnt, work,
-                                                    &P.cnt->err);
+        if (threads == 1024)
+            kb<<<(unsigned)g, threads, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt,
+                                                         max_words, P.W / 32,
+                                                         (int32_t*)(ws + L.chunkcnt), rowcnt, work,
+                                                         &P.cnt->err);
+        else
+            ks<<<(unsigned)g, threads, smem, P.stream>>>(P.d_descs, P.rb, P.nprod, P.rows, P.cnt,
+                                                         max_words, P.W / 32,
+                                                         (int32_t*)(ws + L.chunkcnt), rowcnt, work,
+                                                         &P.cnt->err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
