@@ -215,8 +215,13 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
     // the dense symbolic bitmap (n bits) must fit the per-block shared memory
     P->max_dense_n = (long long)(P->smem_optin - 1024) * 8;
     {
+        // 8-byte values: 1024-column chunks (eight warps per block) up to
+        // 2^18 columns, 2048 beyond (fewer chunks per row; measured faster on
+        // R-MAT 20, slower on R-MAT 18); 4-byte values and patterns: 2048
+        long long widest = 0;
+        for (int p = 0; p < count; ++p) widest = std::max<long long>(widest, B[p].ncols);
         const size_t vbytes = sg::vt_bytes(vt);
-        int cfg = (vbytes == 8) ? 0 : 1;
+        int cfg = (vbytes == 8 && widest <= (1LL << 18)) ? 0 : 1;
         if (o.dense_chunk == sg::kDenseW0) cfg = 0;
         if (o.dense_chunk == sg::kDenseW1) cfg = 1;
         P->W = cfg == 0 ? sg::kDenseW0 : sg::kDenseW1;
