@@ -629,7 +629,7 @@ spgemm_status spgemm_merge_symbolic(int32_t c, const spgemm_csr* parts, const sp
     SG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(sg::DevCounters), s), "merge: memset");
     SG_CUDA(cudaMemsetAsync(rowptrC + m, 0, sizeof(int64_t), s), "merge: memset");
     cudaError_t e = sg::launch_merge(c, parts, vt, m, n, sms, s, false, rowptrC, nullptr, nullptr,
-                                     nullptr, &cnt->err);
+                                     nullptr, &cnt->err, &cnt->work_counter[0]);
     if (e != cudaSuccess) return cuda_fail(e, "merge symbolic");
     e = sg::launch_exclusive_scan(rowptrC, m + 1, temp, s);
     if (e != cudaSuccess) return cuda_fail(e, "merge symbolic: scan");
@@ -658,8 +658,10 @@ spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spg
     if (vt != SPGEMM_BOOL && !valC && m > 0) return fail(SPGEMM_ERR_INVALID_ARG, "valC is NULL");
     sg::DevCounters* cnt = (sg::DevCounters*)ws;
     int sms = device_sm_count(nullptr);
+    SG_CUDA(cudaMemsetAsync(&cnt->work_counter[1], 0, sizeof(unsigned long long),
+                            (cudaStream_t)stream), "merge: memset");
     cudaError_t e = sg::launch_merge(c, parts, vt, m, n, sms, (cudaStream_t)stream, true, nullptr,
-                                     rowptrC, colC, valC, &cnt->err);
+                                     rowptrC, colC, valC, &cnt->err, &cnt->work_counter[1]);
     if (e != cudaSuccess) return cuda_fail(e, "merge numeric");
     return SPGEMM_OK;
 }

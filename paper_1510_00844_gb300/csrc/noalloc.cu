@@ -97,7 +97,7 @@ spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
         return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
     const int vt = pattern ? SPGEMM_BOOL : parts[0].value_type;
     e = sg::launch_merge(c, parts, vt, m, n, sms, s, false, rowptrC, nullptr, nullptr, nullptr,
-                         &cnt->err);
+                         &cnt->err, &cnt->work_counter[0]);
     if (e == cudaSuccess) e = sg::launch_exclusive_scan(rowptrC, m + 1, partials, s);
     int64_t total = 0;
     int herr = 0;
