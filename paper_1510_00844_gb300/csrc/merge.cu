@@ -10,6 +10,8 @@
 // column over the c cursors (lane s holds the cursor of list s).  Up to eight
 // lists take merge_win_kernel, which keeps every list's next entries in
 // flight; more lists take merge_kernel.
+#include <type_traits>
+
 #include "plan.h"
 
 namespace sg {
@@ -22,6 +24,7 @@ struct MergeParts {
     const int64_t* re[kMaxMergeParts];
     const IT* col[kMaxMergeParts];
     const V* val[kMaxMergeParts];
+    long long len[kMaxMergeParts];  // length of col/val of part s
 };
 
 template <class IT, class V, int W, int WARPS, bool NUMERIC>
@@ -118,13 +121,18 @@ __global__ void __launch_bounds__(WARPS * 32)
 }
 
 // The same sum for c <= CM lists with the loads of every list in flight
-// together.  Each list keeps two windows of 32 consecutive entries in
+// together.  Each list keeps three windows of 32 consecutive entries in
 // registers (lane x holds entry x of each): the window being consumed and
-// the next one, whose loads are issued as soon as the previous window comes
-// into use, so a list's next entries arrive while the current ones are
-// accumulated.  Entries are consumed in column order chunk by chunk: the
-// entries of list s inside the chunk are a prefix of what is left of its
-// window (columns ascend), so one ballot per list and window step covers them.
+// the next two; when a window is used up the one after the last is loaded,
+// so a list's next entries arrive while the current ones are accumulated.
+// Entries are consumed in column order chunk by chunk: the entries of list s
+// inside the chunk are a prefix of what is left of its window (columns
+// ascend), so one ballot per list and window step covers them.  Rows are
+// taken from a counter; the count pass only adds up the row's columns.
+template <class V>
+constexpr bool kStoreFirst = std::is_same<V, double>::value || std::is_same<V, float>::value ||
+                             std::is_same<V, int64_t>::value;
+
 template <class IT, class V, int W, int WARPS, bool NUMERIC, int CM>
 __global__ void __launch_bounds__(WARPS * 32)
     merge_win_kernel(int c, MergeParts<IT, V> parts, long long m, long long n,
@@ -159,21 +167,24 @@ __global__ void __launch_bounds__(WARPS * 32)
         long long wb[CM];  // position of window A's first entry (warp-uniform)
         long long we[CM];  // end of list s in row i
         int off[CM];       // entries of window A already consumed
-        long long ja[CM], jb[CM];
-        V va[CM], vb[CM];
+        IT ja[CM], jb[CM], jc[CM];
+        V va[CM], vb[CM], vc[CM];
 #pragma unroll
         for (int s = 0; s < CM; ++s) {
             wb[s] = __shfl_sync(kFull, b_own, s);
             we[s] = s < c ? __shfl_sync(kFull, e_own, s) : 0;
             off[s] = 0;
-            const long long qa = wb[s] + lane, qb = qa + 32;
-            ja[s] = qa < we[s] ? (long long)parts.col[s][qa] : n;
-            jb[s] = qb < we[s] ? (long long)parts.col[s][qb] : n;
+            const long long qa = wb[s] + lane, qb = qa + 32, qc = qa + 64;
+            ja[s] = qa < we[s] ? parts.col[s][qa] : IT(0);
+            jb[s] = qb < we[s] ? parts.col[s][qb] : IT(0);
+            jc[s] = qc < we[s] ? parts.col[s][qc] : IT(0);
             va[s] = V{};
             vb[s] = V{};
+            vc[s] = V{};
             if constexpr (HV) {
                 if (qa < we[s]) va[s] = parts.val[s][qa];
                 if (qb < we[s]) vb[s] = parts.val[s][qb];
+                if (qc < we[s]) vc[s] = parts.val[s][qc];
             }
         }
         long long out = NUMERIC ? rpC[i] : 0;
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             long long nxt = n;
 #pragma unroll
             for (int s = 0; s < CM; ++s) {
-                const long long h = __shfl_sync(kFull, ja[s], off[s] & 31);
+                const long long h = (long long)__shfl_sync(kFull, ja[s], off[s] & 31);
                 if (wb[s] + off[s] < we[s]) nxt = min(nxt, h);
             }
             if (nxt >= n) break;
@@ -192,35 +203,41 @@ __global__ void __launch_bounds__(WARPS * 32)
 #pragma unroll
             for (int s = 0; s < CM; ++s) {
                 while (true) {
-                    const bool valid = lane >= off[s] && ja[s] < c1;
-                    const int slot = (int)(ja[s] - c0);
+                    const bool valid =
+                        lane >= off[s] && wb[s] + lane < we[s] && (long long)ja[s] < c1;
+                    const int slot = (int)((long long)ja[s] - c0);
                     if (valid) {
                         atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                        if constexpr (HV) acc[slot] = VOps<V>::add(acc[slot], va[s]);
+                        if constexpr (HV) {
+                            if (kStoreFirst<V> && s == 0) acc[slot] = va[s];
+                            else acc[slot] = VOps<V>::add(acc[slot], va[s]);
+                        }
                     }
                     __syncwarp();
                     off[s] += __popc(__ballot_sync(kFull, valid));
                     if (off[s] < 32) break;
-                    // window A used up: B moves in, the window after B is loaded
+                    // window A used up: B and C move up, the window after C is loaded
                     wb[s] += 32;
                     off[s] = 0;
                     ja[s] = jb[s];
                     va[s] = vb[s];
-                    const long long qb = wb[s] + 32 + lane;
-                    jb[s] = qb < we[s] ? (long long)parts.col[s][qb] : n;
-                    if constexpr (HV)
-                        if (qb < we[s]) vb[s] = parts.val[s][qb];
+                    jb[s] = jc[s];
+                    vb[s] = vc[s];
+                    const long long qc = wb[s] + 64 + lane;
+                    if (qc < we[s]) {
+                        jc[s] = parts.col[s][qc];
+                        if constexpr (HV) vc[s] = parts.val[s][qc];
+                    }
                     if (wb[s] >= we[s]) break;
                 }
             }
-            // emit (numeric) or count (symbolic) the chunk, clearing it
-            for (int t0 = 0; t0 < NWORDS; t0 += 32) {
-                const int t = t0 + lane;
-                unsigned word = t < NWORDS ? bm[t] : 0u;
-                const int pc = __popc(word);
-                const int incl = warp_incl_scan(pc);
-                const int tot = __shfl_sync(kFull, incl, 31);
-                if constexpr (NUMERIC) {
+            // emit the chunk (numeric) or add up its columns (count), clearing it
+            if constexpr (NUMERIC) {
+                for (int t0 = 0; t0 < NWORDS; t0 += 32) {
+                    const int t = t0 + lane;
+                    unsigned word = t < NWORDS ? bm[t] : 0u;
+                    const int pc = __popc(word);
+                    const int incl = warp_incl_scan(pc);
                     long long pos = out + incl - pc;
                     while (word) {
                         const int b = __ffs(word) - 1;
@@ -233,18 +250,132 @@ __global__ void __launch_bounds__(WARPS * 32)
                         if constexpr (HV) acc[slot] = VOps<V>::init();
                         ++pos;
                     }
+                    if (t < NWORDS) bm[t] = 0u;
+                    out += __shfl_sync(kFull, incl, 31);
                 }
-                if (t < NWORDS) bm[t] = 0u;
-                out += tot;
-                count += tot;
+            } else {
+                // only the row total is needed: per-lane counts, summed once
+                for (int t = lane; t < NWORDS; t += 32) {
+                    count += __popc(bm[t]);
+                    bm[t] = 0u;
+                }
             }
             __syncwarp();
         }
         if constexpr (!NUMERIC) {
+            count = warp_sum(count);
             if (lane == 0) rowcnt[i] = count;
         } else {
             if (lane == 0 && out != out_end) atomicExch(err, (int)kDevCountMismatch);
         }
+    }
+}
+
+// The count of the merge for int32 columns in 16-byte aligned arrays: the
+// same sweep with four columns per lane per load (128 entries per window),
+// so four times the bytes of every list are in flight.  Entry x of a window
+// is component x % 4 of lane x / 4; windows start at multiples of four
+// entries, and entries outside [row begin, row end) are masked by position.
+__device__ __forceinline__ int4 merge_load4(const int32_t* __restrict__ col, long long q,
+                                            long long len) {
+    if (q + 4 <= len) return *reinterpret_cast<const int4*>(col + q);
+    int4 r = make_int4(0, 0, 0, 0);
+    if (q < len) r.x = col[q];
+    if (q + 1 < len) r.y = col[q + 1];
+    if (q + 2 < len) r.z = col[q + 2];
+    if (q + 3 < len) r.w = col[q + 3];
+    return r;
+}
+
+__device__ __forceinline__ int comp4(const int4& v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+template <class V, int W, int WARPS, int CM>
+__global__ void __launch_bounds__(WARPS * 32)
+    merge_count4_kernel(int c, MergeParts<int32_t, V> parts, long long m, long long n,
+                        int64_t* __restrict__ rowcnt, unsigned long long* work) {
+    constexpr int NWORDS = W / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    unsigned* bm = reinterpret_cast<unsigned*>(smem_raw + (size_t)w * (W / 8));
+    for (int t = lane; t < NWORDS; t += 32) bm[t] = 0u;
+    __syncwarp();
+    while (true) {
+        long long i = 0;
+        if (lane == 0) i = (long long)atomicAdd(work, 1ull);
+        i = __shfl_sync(kFull, i, 0);
+        if (i >= m) break;
+        long long b_own = 0, e_own = 0;
+        if (lane < c) {
+            b_own = parts.rp[lane][i];
+            e_own = parts.re[lane] ? parts.re[lane][i] : parts.rp[lane][i + 1];
+        }
+        long long wb[CM], we[CM];
+        int off[CM];
+        int4 xa[CM], xb[CM], xc[CM];
+#pragma unroll
+        for (int s = 0; s < CM; ++s) {
+            const long long b = __shfl_sync(kFull, b_own, s);
+            we[s] = s < c ? __shfl_sync(kFull, e_own, s) : 0;
+            wb[s] = b & ~3LL;
+            off[s] = (int)(b - wb[s]);
+            xa[s] = xb[s] = xc[s] = make_int4(0, 0, 0, 0);
+            if (b < we[s]) {
+                const long long q = wb[s] + 4 * lane;
+                xa[s] = merge_load4(parts.col[s], q, parts.len[s]);
+                if (wb[s] + 128 < we[s]) xb[s] = merge_load4(parts.col[s], q + 128, parts.len[s]);
+                if (wb[s] + 256 < we[s]) xc[s] = merge_load4(parts.col[s], q + 256, parts.len[s]);
+            }
+        }
+        long long count = 0;
+        while (true) {
+            long long nxt = n;
+#pragma unroll
+            for (int s = 0; s < CM; ++s) {
+                const int h = __shfl_sync(kFull, comp4(xa[s], off[s] & 3), (off[s] >> 2) & 31);
+                if (wb[s] + off[s] < we[s]) nxt = min(nxt, (long long)h);
+            }
+            if (nxt >= n) break;
+            const long long c0 = (nxt / W) * W;
+            const long long c1 = min(c0 + (long long)W, n);
+#pragma unroll
+            for (int s = 0; s < CM; ++s) {
+                while (true) {
+                    int got = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int e = 4 * lane + j;
+                        const long long col = comp4(xa[s], j);
+                        const bool valid = e >= off[s] && wb[s] + e < we[s] && col < c1;
+                        if (valid) {
+                            const int slot = (int)(col - c0);
+                            atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                        }
+                        got += __popc(__ballot_sync(kFull, valid));
+                    }
+                    off[s] += got;
+                    if (off[s] < 128) break;
+                    // window A used up: B and C move up, the window after C is loaded
+                    wb[s] += 128;
+                    off[s] = 0;
+                    xa[s] = xb[s];
+                    xb[s] = xc[s];
+                    if (wb[s] + 256 < we[s])
+                        xc[s] = merge_load4(parts.col[s], wb[s] + 256 + 4 * lane, parts.len[s]);
+                    if (wb[s] >= we[s]) break;
+                }
+            }
+            __syncwarp();
+            for (int t = lane; t < NWORDS; t += 32) {
+                count += __popc(bm[t]);
+                bm[t] = 0u;
+            }
+            __syncwarp();
+        }
+        count = warp_sum(count);
+        if (lane == 0) rowcnt[i] = count;
     }
 }
 
@@ -253,11 +384,31 @@ cudaError_t launch_merge_t(int c, const spgemm_csr* parts, long long m, long lon
                            int sm_count, cudaStream_t s, int64_t* rowcnt, const int64_t* rpC,
                            void* colC, void* valC, int* err, unsigned long long* work) {
     MergeParts<IT, V> mp{};
+    bool aligned16 = true;
     for (int t = 0; t < c; ++t) {
         mp.rp[t] = parts[t].rowptr;
         mp.re[t] = parts[t].rowend;
         mp.col[t] = (const IT*)parts[t].col;
         mp.val[t] = (const V*)parts[t].val;
+        mp.len[t] = parts[t].nnz;
+        aligned16 = aligned16 && ((uintptr_t)parts[t].col % 16) == 0;
+    }
+    if constexpr (!NUMERIC && std::is_same<IT, int32_t>::value) {
+        if (c <= 4 && aligned16) {
+            constexpr int W = 8192, WARPS = 4;
+            auto k = c <= 2 ? merge_count4_kernel<V, W, WARPS, 2> : merge_count4_kernel<V, W, WARPS, 4>;
+            const size_t smem = (size_t)WARPS * (W / 8);
+            int occ = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, WARPS * 32, smem);
+            if (occ < 1) occ = 1;
+            const long long need = (m + WARPS - 1) / WARPS;
+            const long long g = std::max<long long>(1, std::min(need, (long long)sm_count * occ));
+            if (m > 0) {
+                count_launches(1);
+                k<<<(unsigned)g, WARPS * 32, smem, s>>>(c, mp, m, n, rowcnt, work);
+            }
+            return cudaGetLastError();
+        }
     }
     if (c <= 8) {
         // the count keeps only a bitmap, so its chunks can be wider
