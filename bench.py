@@ -626,6 +626,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_leg(args):
+    """One workload run `--reps` times with no timing and no JSON line: the
+    command the ncu summaries under profiles/ profile (the first run warms
+    up, so a capture skips its launches)."""
+    import torch
+    from paper_1510_00844_gb300 import amg, inputs, spgemm as sg
+    leg, reps = args.profile_leg, max(1, args.reps)
+    if leg in ("product", "kslice"):
+        dA = sg.to_device(inputs.rmat(args.scale))
+        for _ in range(reps):
+            if leg == "product":
+                nnz = sg.spgemm(dA, dA).nnz
+            else:
+                nnz = sg.spgemm_kslice(dA, dA, 4)[0].nnz
+            torch.cuda.synchronize()
+        print(f"{leg} R-MAT {args.scale}: nnz(C) {nnz}", flush=True)
+    elif leg == "batched":
+        pairs = inputs.batched_er(512)
+        As = [sg.to_device(a) for a, _ in pairs]
+        Bs = [sg.to_device(b) for _, b in pairs]
+        for _ in range(reps):
+            nnz = sum(C.nnz for C in sg.batch_spgemm(As, Bs))
+            torch.cuda.synchronize()
+        print(f"batched 512 ER products: nnz {nnz}", flush=True)
+    elif leg in ("amg", "mis2"):
+        N = 128
+        dA0 = sg.to_device(inputs.laplacian_7pt(N))
+        if leg == "amg":
+            dRs = [sg.to_device(inputs.aggregation_2x2x2(N >> l)) for l in range(3)]
+            chain = amg.GalerkinChain(dA0, dRs, torch.cuda.Stream())
+            chain.capture()
+            for _ in range(reps):
+                chain.replay()
+                torch.cuda.synchronize()
+            chain.check()
+            print("amg: 3-level Galerkin hierarchy of the 128^3 Laplacian, graph replays", reps,
+                  flush=True)
+        else:
+            for _ in range(reps):
+                R, rounds = sg.mis2_restriction(dA0, 20151004)
+                torch.cuda.synchronize()
+            print(f"mis2: {R.ncols} aggregates in {rounds} rounds", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -640,7 +684,14 @@ def main():
                     help="add five MCL steps on R-MAT 20 to the learned-sizing leg (about 9 min)")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the split / batched / AMG comparisons")
+    ap.add_argument("--profile-leg", choices=["product", "kslice", "batched", "amg", "mis2"],
+                    help="run one workload --reps times without timing (for ncu captures)")
+    ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of --profile-leg")
+    ap.add_argument("--reps", type=int, default=2, help="runs of --profile-leg")
     args = ap.parse_args()
+    if args.profile_leg:
+        run_profile_leg(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
