@@ -229,6 +229,27 @@ def test_merge_integer_and_bool(sg):
     assert_pattern_equal(Cb, R)
 
 
+def test_merge_unaligned_column_arrays(sg):
+    """Partials whose int32 column arrays do not start on a 16-byte boundary
+    are counted one column per lane (the four-column loads need aligned
+    arrays); the merged product is still the oracle's sum of the partials."""
+    import torch
+
+    A = inputs.rmat(11)
+    dA = sg.to_device(A)
+    _, parts = sg.spgemm_kslice(dA, dA, 4, verify=True)
+    shifted = []
+    for P in parts:
+        buf = torch.empty(P.col.numel() + 1, dtype=P.col.dtype, device=P.col.device)
+        buf[1:] = P.col
+        shifted.append(sg.DeviceCSR(P.nrows, P.ncols, P.rowptr, buf[1:], P.val))
+    assert shifted[0].col.data_ptr() % 16 != 0
+    C = sg.merge(shifted, verify=True)
+    S = oracle.sum_partials([oracle.spgemm(As, Bs) for As, Bs in oracle.kslice(A, A, 4)])
+    assert_pattern_equal(C, S)
+    assert np.array_equal(C.to_host()[2], S.val)
+
+
 def test_rmat_scale18_sampled_rows(sg):
     """The full R-MAT scale-18 squaring in the benchmark's launch
     configuration; a seeded sample of rows (including the largest-flops rows)
