@@ -9,7 +9,9 @@
 // order.  Chunks no list touches are skipped by jumping to the smallest next
 // column over the c cursors (lane s holds the cursor of list s).  Up to eight
 // lists take merge_win_kernel, which keeps every list's next entries in
-// flight; more lists take merge_kernel.
+// flight; more lists take merge_kernel.  The count pass of up to four int32
+// lists in 16-byte aligned arrays takes merge_count4_kernel (four columns
+// per lane per load).
 #include <type_traits>
 
 #include "plan.h"
