@@ -390,7 +390,10 @@ size_t spgemm_merge_workspace_size(int32_t c, int64_t m, int64_t n);
 
 /* spgemm_merge_symbolic -- parts[0..c-1]: c partial products of equal shape
  * (sorted rows).  Writes rowptrC (int64[m+1]) of C = sum_s parts[s] and
- * nnz(C) (host).  Waits for the stream. */
+ * nnz(C) (host).  Waits for the stream.  Performance only: with c <= 4 and
+ * int32 column arrays whose addresses are multiples of 16 bytes, the count
+ * reads four columns per lane per load; each part's nnz must then be the
+ * length of its col array (as stated for spgemm_csr). */
 spgemm_status spgemm_merge_symbolic(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
                                     void* stream, void* ws, size_t ws_bytes, int64_t* rowptrC,
                                     int64_t* nnz_c);
