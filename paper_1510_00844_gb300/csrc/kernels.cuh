@@ -608,12 +608,113 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int64_t* rpB = c.rpB;
         const IT* ciB = c.ciB;
         const V* vB = c.vB;
+        // A row of at most 32 A entries has its one batch loaded here, once.
+        // If its products hardly repeat a column (nnz(C(i,:)) >= 3/4 of its
+        // flops, known exactly outside slot mode) and fit half the table, it
+        // is expanded, sorted and compressed instead of hashed: products go
+        // to the table's lower half in ascending k, a stable radix sort by
+        // column keeps that order among equal columns, and each run of equal
+        // columns is reduced from the identity in that order, as the hash
+        // path would.
+        bool pre = false;
+        long long lo_p = 0;
+        int len_p = 0;
+        V a_p = VOps<V>::init();
+        if constexpr (LOG2T >= 10) {
+            if (!slot_mode && a1 > a0 && a1 - a0 <= 32) {
+                const int nb = (int)(a1 - a0);
+                if (lane < nb) {
+                    const long long k = (long long)ciA[a0 + lane];
+                    lo_p = rpB[k];
+                    len_p = (int)(rpB[k + 1] - lo_p);
+                    a_p = load_val(vA, a0 + lane);
+                }
+                pre = true;
+                const long long fl = warp_sum((long long)len_p);
+                const long long nz = rpC[r + 1] - rpC[r];
+                if (fl <= T / 2 && 4 * nz >= 3 * fl) {
+                    int nf = 0;
+                    walk_batch4(nb, lo_p, len_p, [&](const long long (&q)[4], const int (&e)[4],
+                                                     const bool (&vl)[4], bool) {
+                        K key[4];
+                        V bq[4];
+                        V ae[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            ae[t] = shfl_val(a_p, e[t]);
+                            key[t] = K(0);
+                            bq[t] = V{};
+                            if (vl[t]) {
+                                key[t] = (K)ciB[q[t]];
+                                bq[t] = load_val(vB, q[t]);
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            // the valid lanes of a round are a prefix of the warp
+                            if (vl[t]) {
+                                keys[nf + lane] = key[t];
+                                if constexpr (HV) acc[nf + lane] = VOps<V>::mul(ae[t], bq[t]);
+                            }
+                            nf += __popc(__ballot_sync(kFull, vl[t]));
+                        }
+                    });
+                    __syncwarp();
+                    const int bits = c.n > 1 ? 64 - __clzll((unsigned long long)(c.n - 1)) : 1;
+                    const bool up = warp_radix_sort<K, V>(keys, acc, keys + T / 2, acc + T / 2, nf,
+                                                          bits, rcnt_smem);
+                    const K* sk = up ? keys + T / 2 : keys;
+                    const V* sv = up ? acc + T / 2 : acc;
+                    const long long out = rpC[r];
+                    int outp = 0;
+                    for (int i0 = 0; i0 < nf; i0 += 32) {
+                        const int i = i0 + lane;
+                        const bool in = i < nf;
+                        const K kk = in ? sk[i] : K(0);
+                        const bool start = in && (i == 0 || sk[i - 1] != kk);
+                        const unsigned sm = __ballot_sync(kFull, start);
+                        if (start) {
+                            V sum = VOps<V>::init();
+                            if constexpr (HV) {
+                                sum = VOps<V>::add(sum, sv[i]);
+                                for (int j = i + 1; j < nf && sk[j] == kk; ++j)
+                                    sum = VOps<V>::add(sum, sv[j]);
+                            }
+                            const long long pq = out + outp + __popc(sm & lanemask_lt());
+                            if (pq < cap) {
+                                ciC[pq] = (IT)kk;
+                                if constexpr (HV) vC[pq] = sum;
+                            }
+                        }
+                        outp += __popc(sm);
+                    }
+                    if (lane == 0 && (long long)outp != nz) atomicExch(err, (int)kDevCountMismatch);
+                    if (lane == 0 && out + outp > cap) atomicExch(err, (int)kDevCapacity);
+                    __syncwarp();
+                    // both halves back to the empty table
+                    for (int t = lane; t < nf; t += 32) {
+                        keys[t] = K(-1);
+                        keys[T / 2 + t] = K(-1);
+                        if constexpr (HV) {
+                            acc[t] = VOps<V>::init();
+                            acc[T / 2 + t] = VOps<V>::init();
+                        }
+                    }
+                    __syncwarp();
+                    continue;
+                }
+            }
+        }
         for (long long b = a0; b < a1; b += 32) {
             const int nb = (int)min(32LL, a1 - b);
             long long lo = 0;
             int len = 0;
             V a = VOps<V>::init();
-            if (lane < nb) {
+            if (pre) {  // the row's single batch, loaded above
+                lo = lo_p;
+                len = len_p;
+                a = a_p;
+            } else if (lane < nb) {
                 long long k = (long long)ciA[b + lane];
                 lo = rpB[k];
                 len = (int)(rpB[k + 1] - lo);
