@@ -107,6 +107,58 @@ static int threads_or_default(int nthreads) {
 
 int oracle_num_threads(int nthreads) { return threads_or_default(nthreads); }
 
+static int thread_index(void) {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+/* Per-thread SPA buffers (stamp, list of touched columns, value arrays),
+ * allocated before a parallel region: an allocation failure is then reported
+ * before any thread starts, instead of one thread skipping the work-sharing
+ * loop that the others enter. */
+typedef struct {
+    int64_t* stamp;
+    int64_t* list;
+    double* spa_d;
+    uint64_t* spa_i;
+} spa_buf;
+
+static void free_bufs(spa_buf* b, int nt) {
+    if (!b) return;
+    for (int t = 0; t < nt; ++t) {
+        free(b[t].stamp);
+        free(b[t].list);
+        free(b[t].spa_d);
+        free(b[t].spa_i);
+    }
+    free(b);
+}
+
+/* nt buffers over n columns; lists and value arrays only when `fill`. */
+static spa_buf* alloc_bufs(int nt, int64_t n, int fill, int vtype) {
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    spa_buf* b = (spa_buf*)calloc((size_t)nt, sizeof(spa_buf));
+    if (!b) return NULL;
+    for (int t = 0; t < nt; ++t) {
+        b[t].stamp = (int64_t*)malloc(sizeof(int64_t) * nn);
+        int ok = b[t].stamp != NULL;
+        if (fill) {
+            b[t].list = (int64_t*)malloc(sizeof(int64_t) * nn);
+            ok = ok && b[t].list != NULL;
+            if (is_f64(vtype)) ok = ok && (b[t].spa_d = (double*)malloc(sizeof(double) * nn));
+            if (is_i64(vtype)) ok = ok && (b[t].spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn));
+        }
+        if (!ok) {
+            free_bufs(b, nt);
+            return NULL;
+        }
+    }
+    return b;
+}
+
 /* flops(A,B) per row: the number of scalar multiplications,
  * flops_i = sum_{k in A(i,:)} nnz(B(k,:))  (Sec. 2 "Notation"). */
 int64_t oracle_row_flops(int64_t m, const int64_t* rpA, const int64_t* ciA,
@@ -130,36 +182,32 @@ int64_t oracle_spgemm_count(int64_t m, int64_t n, const int64_t* rpA, const int6
                             const int64_t* rpB, const int64_t* ciB, int64_t* rowcnt,
                             int nthreads) {
     int nt = threads_or_default(nthreads);
-    int failed = 0;
+    spa_buf* bufs = alloc_bufs(nt, n, 0, ORACLE_BOOL);
+    if (!bufs) return -1;
     int64_t total = 0;
 #pragma omp parallel num_threads(nt) reduction(+ : total)
     {
-        int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-        if (!stamp) {
-#pragma omp atomic write
-            failed = 1;
-        } else {
-            for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
+        int64_t* stamp = bufs[thread_index()].stamp;
+        for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
 #pragma omp for schedule(dynamic, 64)
-            for (int64_t i = 0; i < m; ++i) {
-                int64_t cnt = 0;
-                for (int64_t p = rpA[i]; p < rpA[i + 1]; ++p) {
-                    int64_t k = ciA[p];
-                    for (int64_t q = rpB[k]; q < rpB[k + 1]; ++q) {
-                        int64_t j = ciB[q];
-                        if (stamp[j] != i) {
-                            stamp[j] = i;
-                            ++cnt;
-                        }
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t cnt = 0;
+            for (int64_t p = rpA[i]; p < rpA[i + 1]; ++p) {
+                int64_t k = ciA[p];
+                for (int64_t q = rpB[k]; q < rpB[k + 1]; ++q) {
+                    int64_t j = ciB[q];
+                    if (stamp[j] != i) {
+                        stamp[j] = i;
+                        ++cnt;
                     }
                 }
-                rowcnt[i] = cnt;
-                total += cnt;
             }
-            free(stamp);
+            rowcnt[i] = cnt;
+            total += cnt;
         }
     }
-    return failed ? -1 : total;
+    free_bufs(bufs, nt);
+    return total;
 }
 
 /* Fill colC/valC given rpC (exclusive scan of the row counts).  Returns 0, or
@@ -168,68 +216,60 @@ int oracle_spgemm_fill(int64_t m, int64_t n, const int64_t* rpA, const int64_t* 
                        const void* vA, const int64_t* rpB, const int64_t* ciB, const void* vB,
                        int vtype, const int64_t* rpC, int64_t* ciC, void* vC, int nthreads) {
     int nt = threads_or_default(nthreads);
+    spa_buf* bufs = alloc_bufs(nt, n, 1, vtype);
+    if (!bufs) return -1;
     int status = 0;
 #pragma omp parallel num_threads(nt)
     {
-        size_t nn = (size_t)(n > 0 ? n : 1);
-        int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * nn);
-        int64_t* list = (int64_t*)malloc(sizeof(int64_t) * nn);
-        double* spa_d = NULL;
-        uint64_t* spa_i = NULL;
-        if (is_f64(vtype)) spa_d = (double*)malloc(sizeof(double) * nn);
-        if (is_i64(vtype)) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
-        if (!stamp || !list || (is_f64(vtype) && !spa_d) || (is_i64(vtype) && !spa_i)) {
-#pragma omp atomic write
-            status = -1;
-        } else {
-            const double* aD = (const double*)vA;
-            const double* bD = (const double*)vB;
-            const uint64_t* aI = (const uint64_t*)vA;
-            const uint64_t* bI = (const uint64_t*)vB;
-            double* cD = (double*)vC;
-            uint64_t* cI = (uint64_t*)vC;
-            for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
+        spa_buf* my = &bufs[thread_index()];
+        int64_t* stamp = my->stamp;
+        int64_t* list = my->list;
+        double* spa_d = my->spa_d;
+        uint64_t* spa_i = my->spa_i;
+        const double* aD = (const double*)vA;
+        const double* bD = (const double*)vB;
+        const uint64_t* aI = (const uint64_t*)vA;
+        const uint64_t* bI = (const uint64_t*)vB;
+        double* cD = (double*)vC;
+        uint64_t* cI = (uint64_t*)vC;
+        for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
 #pragma omp for schedule(dynamic, 64)
-            for (int64_t i = 0; i < m; ++i) {
-                int64_t nz = 0;
-                for (int64_t p = rpA[i]; p < rpA[i + 1]; ++p) {
-                    int64_t k = ciA[p];
-                    for (int64_t q = rpB[k]; q < rpB[k + 1]; ++q) {
-                        int64_t j = ciB[q];
-                        int first = stamp[j] != i;
-                        if (first) {
-                            stamp[j] = i;
-                            list[nz++] = j;
-                        }
-                        if (is_f64(vtype)) {
-                            double prod = mul_d(vtype, aD[p], bD[q]);
-                            spa_d[j] = add_d(vtype, first, spa_d[j], prod);
-                        } else if (is_i64(vtype)) {
-                            uint64_t prod = mul_i(vtype, aI[p], bI[q]);
-                            spa_i[j] = add_i(vtype, first, spa_i[j], prod);
-                        }
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t nz = 0;
+            for (int64_t p = rpA[i]; p < rpA[i + 1]; ++p) {
+                int64_t k = ciA[p];
+                for (int64_t q = rpB[k]; q < rpB[k + 1]; ++q) {
+                    int64_t j = ciB[q];
+                    int first = stamp[j] != i;
+                    if (first) {
+                        stamp[j] = i;
+                        list[nz++] = j;
+                    }
+                    if (is_f64(vtype)) {
+                        double prod = mul_d(vtype, aD[p], bD[q]);
+                        spa_d[j] = add_d(vtype, first, spa_d[j], prod);
+                    } else if (is_i64(vtype)) {
+                        uint64_t prod = mul_i(vtype, aI[p], bI[q]);
+                        spa_i[j] = add_i(vtype, first, spa_i[j], prod);
                     }
                 }
-                if (nz != rpC[i + 1] - rpC[i]) {
+            }
+            if (nz != rpC[i + 1] - rpC[i]) {
 #pragma omp atomic write
-                    status = -2;
-                    continue;
-                }
-                qsort(list, (size_t)nz, sizeof(int64_t), cmp_i64);
-                int64_t base = rpC[i];
-                for (int64_t t = 0; t < nz; ++t) {
-                    int64_t j = list[t];
-                    ciC[base + t] = j;
-                    if (is_f64(vtype)) cD[base + t] = spa_d[j];
-                    else if (is_i64(vtype)) cI[base + t] = spa_i[j];
-                }
+                status = -2;
+                continue;
+            }
+            qsort(list, (size_t)nz, sizeof(int64_t), cmp_i64);
+            int64_t base = rpC[i];
+            for (int64_t t = 0; t < nz; ++t) {
+                int64_t j = list[t];
+                ciC[base + t] = j;
+                if (is_f64(vtype)) cD[base + t] = spa_d[j];
+                else if (is_i64(vtype)) cI[base + t] = spa_i[j];
             }
         }
-        free(stamp);
-        free(list);
-        free(spa_d);
-        free(spa_i);
     }
+    free_bufs(bufs, nt);
     return status;
 }
 
@@ -238,93 +278,81 @@ int oracle_spgemm_fill(int64_t m, int64_t n, const int64_t* rpA, const int64_t* 
 int64_t oracle_sum_count(int c, int64_t m, int64_t n, const int64_t* const* rps,
                          const int64_t* const* cis, int64_t* rowcnt, int nthreads) {
     int nt = threads_or_default(nthreads);
-    int failed = 0;
+    spa_buf* bufs = alloc_bufs(nt, n, 0, ORACLE_BOOL);
+    if (!bufs) return -1;
     int64_t total = 0;
 #pragma omp parallel num_threads(nt) reduction(+ : total)
     {
-        int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-        if (!stamp) {
-#pragma omp atomic write
-            failed = 1;
-        } else {
-            for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
+        int64_t* stamp = bufs[thread_index()].stamp;
+        for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
 #pragma omp for schedule(dynamic, 64)
-            for (int64_t i = 0; i < m; ++i) {
-                int64_t cnt = 0;
-                for (int s = 0; s < c; ++s)
-                    for (int64_t q = rps[s][i]; q < rps[s][i + 1]; ++q) {
-                        int64_t j = cis[s][q];
-                        if (stamp[j] != i) {
-                            stamp[j] = i;
-                            ++cnt;
-                        }
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t cnt = 0;
+            for (int s = 0; s < c; ++s)
+                for (int64_t q = rps[s][i]; q < rps[s][i + 1]; ++q) {
+                    int64_t j = cis[s][q];
+                    if (stamp[j] != i) {
+                        stamp[j] = i;
+                        ++cnt;
                     }
-                rowcnt[i] = cnt;
-                total += cnt;
-            }
-            free(stamp);
+                }
+            rowcnt[i] = cnt;
+            total += cnt;
         }
     }
-    return failed ? -1 : total;
+    free_bufs(bufs, nt);
+    return total;
 }
 
 int oracle_sum_fill(int c, int64_t m, int64_t n, const int64_t* const* rps,
                     const int64_t* const* cis, const void* const* vs, int vtype,
                     const int64_t* rpC, int64_t* ciC, void* vC, int nthreads) {
     int nt = threads_or_default(nthreads);
+    spa_buf* bufs = alloc_bufs(nt, n, 1, vtype);
+    if (!bufs) return -1;
     int status = 0;
 #pragma omp parallel num_threads(nt)
     {
-        size_t nn = (size_t)(n > 0 ? n : 1);
-        int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * nn);
-        int64_t* list = (int64_t*)malloc(sizeof(int64_t) * nn);
-        double* spa_d = NULL;
-        uint64_t* spa_i = NULL;
-        if (is_f64(vtype)) spa_d = (double*)malloc(sizeof(double) * nn);
-        if (is_i64(vtype)) spa_i = (uint64_t*)malloc(sizeof(uint64_t) * nn);
-        if (!stamp || !list || (is_f64(vtype) && !spa_d) || (is_i64(vtype) && !spa_i)) {
-#pragma omp atomic write
-            status = -1;
-        } else {
-            double* cD = (double*)vC;
-            uint64_t* cI = (uint64_t*)vC;
-            for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
+        spa_buf* my = &bufs[thread_index()];
+        int64_t* stamp = my->stamp;
+        int64_t* list = my->list;
+        double* spa_d = my->spa_d;
+        uint64_t* spa_i = my->spa_i;
+        double* cD = (double*)vC;
+        uint64_t* cI = (uint64_t*)vC;
+        for (int64_t j = 0; j < n; ++j) stamp[j] = -1;
 #pragma omp for schedule(dynamic, 64)
-            for (int64_t i = 0; i < m; ++i) {
-                int64_t nz = 0;
-                for (int s = 0; s < c; ++s) {
-                    const double* vd = (const double*)vs[s];
-                    const uint64_t* vi = (const uint64_t*)vs[s];
-                    for (int64_t q = rps[s][i]; q < rps[s][i + 1]; ++q) {
-                        int64_t j = cis[s][q];
-                        int first = stamp[j] != i;
-                        if (first) {
-                            stamp[j] = i;
-                            list[nz++] = j;
-                        }
-                        if (is_f64(vtype)) spa_d[j] = add_d(vtype, first, spa_d[j], vd[q]);
-                        else if (is_i64(vtype)) spa_i[j] = add_i(vtype, first, spa_i[j], vi[q]);
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t nz = 0;
+            for (int s = 0; s < c; ++s) {
+                const double* vd = (const double*)vs[s];
+                const uint64_t* vi = (const uint64_t*)vs[s];
+                for (int64_t q = rps[s][i]; q < rps[s][i + 1]; ++q) {
+                    int64_t j = cis[s][q];
+                    int first = stamp[j] != i;
+                    if (first) {
+                        stamp[j] = i;
+                        list[nz++] = j;
                     }
-                }
-                if (nz != rpC[i + 1] - rpC[i]) {
-#pragma omp atomic write
-                    status = -2;
-                    continue;
-                }
-                qsort(list, (size_t)nz, sizeof(int64_t), cmp_i64);
-                int64_t base = rpC[i];
-                for (int64_t t = 0; t < nz; ++t) {
-                    int64_t j = list[t];
-                    ciC[base + t] = j;
-                    if (is_f64(vtype)) cD[base + t] = spa_d[j];
-                    else if (is_i64(vtype)) cI[base + t] = spa_i[j];
+                    if (is_f64(vtype)) spa_d[j] = add_d(vtype, first, spa_d[j], vd[q]);
+                    else if (is_i64(vtype)) spa_i[j] = add_i(vtype, first, spa_i[j], vi[q]);
                 }
             }
+            if (nz != rpC[i + 1] - rpC[i]) {
+#pragma omp atomic write
+                status = -2;
+                continue;
+            }
+            qsort(list, (size_t)nz, sizeof(int64_t), cmp_i64);
+            int64_t base = rpC[i];
+            for (int64_t t = 0; t < nz; ++t) {
+                int64_t j = list[t];
+                ciC[base + t] = j;
+                if (is_f64(vtype)) cD[base + t] = spa_d[j];
+                else if (is_i64(vtype)) cI[base + t] = spa_i[j];
+            }
         }
-        free(stamp);
-        free(list);
-        free(spa_d);
-        free(spa_i);
     }
+    free_bufs(bufs, nt);
     return status;
 }

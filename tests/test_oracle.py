@@ -295,6 +295,23 @@ def test_mcl_prune_renorm():
             assert abs(Q.val[a:b].sum() - 1.0) <= 1e-13
 
 
+def test_mcl_prune_keeps_entries_equal_to_threshold():
+    """Pruning drops entries strictly below the threshold: an entry exactly at
+    1e-4 stays.  Hand-written 2 x 4 case: row 0 holds 1e-4 (kept), 9.9e-5
+    (dropped) and 0.5 (kept); row 1 holds only 9.99e-5 (dropped), so it ends
+    empty.  Kept row 0 renormalised: 1e-4 / (1e-4 + 0.5) and 0.5 / (1e-4 +
+    0.5), the sum taken left to right."""
+    C = oracle.OCSR(2, 4, np.array([0, 3, 4], dtype=np.int64),
+                    np.array([0, 1, 3, 2], dtype=np.int64),
+                    np.array([1e-4, 9.9e-5, 0.5, 9.99e-5]))
+    Q = oracle.mcl_prune_renorm(C, 1e-4)
+    assert Q.nnz == 2                                       # written by hand: 1e-4 and 0.5 survive
+    assert list(Q.rowptr) == [0, 2, 2]
+    assert list(Q.col) == [0, 3]
+    s = 1e-4 + 0.5
+    assert Q.val[0] == 1e-4 / s and Q.val[1] == 0.5 / s
+
+
 # ------------------------------------------------------------ min semirings
 # (min, +) and (min, select2nd): the operations MIS-2 aggregation is built
 # from (Alg. 3).  A min reduction starts at +inf (int64: INT64_MAX) and keeps
