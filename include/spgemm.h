@@ -225,6 +225,25 @@ spgemm_status spgemm_sizer_train(const float* X, const float* T, const int64_t* 
 /* Row features (F = 6, device float [rows x 6]) of a plan's rows, the
  * predictor's input, for building training sets.  No wait. */
 spgemm_status spgemm_row_features(spgemm_plan_t plan, float* X);
+/* Training targets T[i] = log2(1 + rowptrC[i+1] - rowptrC[i]) (device float
+ * [m]) from the row pointers of the exact symbolic phase.  No wait. */
+spgemm_status spgemm_sizer_targets(const int64_t* rowptrC, int64_t m, float* T, void* stream);
+/* Trained predictor to a host byte record, so that it can be reused by
+ * another process: magic "SGSIZER", format version 1, F, hidden width 32,
+ * feature set 1 (the six features above, in that order), target 1
+ * (log2(1 + nnz)), parameter count, the float32 parameters (device array,
+ * copied on `stream`; the call waits for it), then a 64-bit FNV-1a hash of the
+ * preceding bytes; little-endian.  *bytes_out = record size; with buf NULL
+ * only the size is returned.  INVALID_ARG if buf_bytes is too small. */
+spgemm_status spgemm_sizer_save(const float* params, int32_t F, void* stream, void* buf,
+                                size_t buf_bytes, size_t* bytes_out);
+/* Reads a record written by spgemm_sizer_save into params (device array of
+ * spgemm_sizer_param_count(F) floats; waits for the copy).  INVALID_ARG for
+ * a wrong magic, F, network shape, feature set, target, a truncated record or
+ * a hash mismatch; NOT_SUPPORTED for another format version.  params is left
+ * untouched on any error. */
+spgemm_status spgemm_sizer_load(const void* buf, size_t buf_bytes, int32_t F, float* params,
+                                void* stream);
 
 /* Device allocation callback: returns `bytes` (>= 256-byte aligned) of
  * device memory owned by the caller, or NULL. */
@@ -416,8 +435,10 @@ spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spg
  * Limits: at most 2^24 rows (INVALID_ARG beyond).  All calls on a device
  * share the array, which keeps the last call's contents (the error word is
  * cleared at the start of each call); calls that overlap on the GPU race on
- * it.  The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture. */
+ * it.  Arguments are checked as by spgemm_merge_symbolic.  The first call on
+ * a device looks up the array's device address (with that device current),
+ * and a call after the device's context changed (a device reset) looks it up
+ * again; make that first call before any stream capture. */
 spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
                                            const spgemm_opts* opts, void* stream,
                                            int64_t* rowptrC, int64_t* nnz_c);

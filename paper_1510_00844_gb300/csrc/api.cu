@@ -402,6 +402,32 @@ using sg::make_plan;
 using sg::check_ws;
 using sg::run_numeric;
 
+namespace sg {
+// The argument checks of the merge entry points (shared with the
+// allocation-free count in noalloc.cu).
+spgemm_status check_merge_parts(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                int* vt_out) {
+    if (c < 1 || c > 32) return fail(SPGEMM_ERR_INVALID_ARG, "merge needs 1 <= c <= 32 parts (c = %d)", c);
+    if (!parts) return fail(SPGEMM_ERR_INVALID_ARG, "parts is NULL");
+    spgemm_opts o{};
+    if (opts) o = *opts;
+    if (spgemm_status st0 = check_semiring(o, &parts[0]); st0 != SPGEMM_OK) return st0;
+    const int vt = kernel_value_type(&parts[0], &o);
+    for (int s = 0; s < c; ++s) {
+        spgemm_status st = check_csr(&parts[s], "part", vt != SPGEMM_BOOL);
+        if (st != SPGEMM_OK) return st;
+        if (parts[s].nrows != parts[0].nrows || parts[s].ncols != parts[0].ncols)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d shape differs from part 0", s);
+        if (parts[s].index_type != parts[0].index_type)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d index type differs", s);
+        if (vt != SPGEMM_BOOL && parts[s].value_type != parts[0].value_type)
+            return fail(SPGEMM_ERR_INVALID_ARG, "part %d value type differs", s);
+    }
+    *vt_out = vt;
+    return SPGEMM_OK;
+}
+}  // namespace sg
+
 extern "C" {
 
 int64_t spgemm_kernel_launches(void) { return sg::g_launches.load(); }
@@ -586,34 +612,13 @@ size_t spgemm_merge_workspace_size(int32_t c, int64_t m, int64_t n) {
     return align_up(sizeof(sg::DevCounters)) + align_up(sg::scan_temp_bytes(m + 1));
 }
 
-static spgemm_status check_parts(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
-                                 int* vt_out) {
-    if (c < 1 || c > 32) return fail(SPGEMM_ERR_INVALID_ARG, "merge needs 1 <= c <= 32 parts (c = %d)", c);
-    if (!parts) return fail(SPGEMM_ERR_INVALID_ARG, "parts is NULL");
-    spgemm_opts o{};
-    if (opts) o = *opts;
-    if (spgemm_status st0 = check_semiring(o, &parts[0]); st0 != SPGEMM_OK) return st0;
-    const int vt = kernel_value_type(&parts[0], &o);
-    for (int s = 0; s < c; ++s) {
-        spgemm_status st = check_csr(&parts[s], "part", vt != SPGEMM_BOOL);
-        if (st != SPGEMM_OK) return st;
-        if (parts[s].nrows != parts[0].nrows || parts[s].ncols != parts[0].ncols)
-            return fail(SPGEMM_ERR_INVALID_ARG, "part %d shape differs from part 0", s);
-        if (parts[s].index_type != parts[0].index_type)
-            return fail(SPGEMM_ERR_INVALID_ARG, "part %d index type differs", s);
-        if (vt != SPGEMM_BOOL && parts[s].value_type != parts[0].value_type)
-            return fail(SPGEMM_ERR_INVALID_ARG, "part %d value type differs", s);
-    }
-    *vt_out = vt;
-    return SPGEMM_OK;
-}
 
 spgemm_status spgemm_merge_symbolic(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
                                     void* stream, void* ws, size_t ws_bytes, int64_t* rowptrC,
                                     int64_t* nnz_c) {
     g_last_error.clear();
     int vt = 0;
-    spgemm_status st = check_parts(c, parts, opts, &vt);
+    spgemm_status st = sg::check_merge_parts(c, parts, opts, &vt);
     if (st != SPGEMM_OK) return st;
     if (!rowptrC || !nnz_c) return fail(SPGEMM_ERR_INVALID_ARG, "NULL output");
     const long long m = parts[0].nrows, n = parts[0].ncols;
@@ -646,7 +651,7 @@ spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spg
                                    const int64_t* rowptrC, void* colC, void* valC) {
     g_last_error.clear();
     int vt = 0;
-    spgemm_status st = check_parts(c, parts, opts, &vt);
+    spgemm_status st = sg::check_merge_parts(c, parts, opts, &vt);
     if (st != SPGEMM_OK) return st;
     if (!rowptrC) return fail(SPGEMM_ERR_INVALID_ARG, "rowptrC is NULL");
     const long long m = parts[0].nrows, n = parts[0].ncols;

@@ -12,11 +12,14 @@
 // * every call on a device uses the same array, which keeps the last call's
 //   contents (the error word is cleared at the start of each call); calls
 //   that overlap on the GPU (other threads, other streams) race on it;
-// * the array's device address is looked up once per device, with that
-//   device current, by the first call made on it; make that first call
-//   before any stream capture.
+// * the array's device address is looked up by the first call made on a
+//   device, with that device current, and again whenever the device's
+//   context has changed since (after a device reset, say); make that first
+//   call before any stream capture.
 #include <cstdio>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "plan.h"
 
@@ -35,24 +38,57 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context the address belongs to
 
 spgemm_status static_fail(spgemm_status st, const char* msg) {
     sg::set_last_error(msg);
     return st;
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Unique id of the calling thread's current context (ids are never reused
+// within a process, so a reset device's new context has a new one); 0 when
+// there is no current context or the driver entry points are unavailable.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: looked up once
+// per device and context, and on every call when the context id is unknown.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+        // the lookup made the device's context current if none was
+        g_scratch_ctx[dev] = ctx ? ctx : current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -66,21 +102,15 @@ spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
                                            const spgemm_opts* opts, void* stream,
                                            int64_t* rowptrC, int64_t* nnz_c) {
     sg::set_last_error("");
-    if (c < 1 || c > 32 || !parts || !rowptrC || !nnz_c)
-        return static_fail(SPGEMM_ERR_INVALID_ARG, "need 1 <= c <= 32 parts and non-NULL outputs");
+    // the same argument checks as spgemm_merge_symbolic
+    int vt = 0;
+    spgemm_status st = sg::check_merge_parts(c, parts, opts, &vt);
+    if (st != SPGEMM_OK) return st;
+    if (!rowptrC || !nnz_c) return static_fail(SPGEMM_ERR_INVALID_ARG, "NULL output");
     const long long m = parts[0].nrows, n = parts[0].ncols;
-    if (m < 0 || m > kStaticMaxRows)
+    if (m > kStaticMaxRows)
         return static_fail(SPGEMM_ERR_INVALID_ARG,
                            "row count outside the static scratch limit (at most 16777216 rows)");
-    spgemm_opts o{};
-    if (opts) o = *opts;
-    const bool pattern = o.semiring == SPGEMM_OR_AND || parts[0].value_type == SPGEMM_BOOL;
-    for (int s = 0; s < c; ++s) {
-        const spgemm_csr& P = parts[s];
-        if (P.nrows != m || P.ncols != n || P.index_type != parts[0].index_type || !P.rowptr ||
-            (P.nnz > 0 && !P.col))
-            return static_fail(SPGEMM_ERR_INVALID_ARG, "parts differ in shape or index type, or miss arrays");
-    }
     void* base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
@@ -95,7 +125,6 @@ spgemm_status spgemm_merge_symbolic_static(int32_t c, const spgemm_csr* parts,
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(sg::DevCounters), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(rowptrC + m, 0, sizeof(int64_t), s)) != cudaSuccess)
         return static_fail(SPGEMM_ERR_CUDA, cudaGetErrorString(e));
-    const int vt = pattern ? SPGEMM_BOOL : parts[0].value_type;
     e = sg::launch_merge(c, parts, vt, m, n, sms, s, false, rowptrC, nullptr, nullptr, nullptr,
                          &cnt->err, &cnt->work_counter[0]);
     if (e == cudaSuccess) e = sg::launch_exclusive_scan(rowptrC, m + 1, partials, s);

@@ -102,6 +102,10 @@ spgemm_status make_plan(int32_t count, const spgemm_csr* A, const spgemm_csr* B,
                         bool device_sized, spgemm_plan_t* plan_out, const float* sizer_params,
                         float sizer_margin);
 spgemm_status check_ws(spgemm_plan_t P, void* ws, size_t ws_bytes);
+// Checks of the merge arguments (count of parts, shapes, index and value
+// types, semiring); *vt_out = the value kind the merge kernels use.
+spgemm_status check_merge_parts(int32_t c, const spgemm_csr* parts, const spgemm_opts* opts,
+                                int* vt_out);
 cudaError_t run_numeric(Plan* P, unsigned char* w, const int64_t* rowptrC, long long cap,
                         void* colC, void* valC);
 
