@@ -9,6 +9,7 @@
 // global gradient.  Adam updates the parameters.  Parameter layout: W1
 // (32 x F, row-major), b1, W2 (32 x 32, row-major), b2, w3, b3.
 #include <cstdio>
+#include <cstring>
 
 #include "plan.h"
 
@@ -179,6 +180,37 @@ cudaError_t launch_sizer_grad(const float* X, const float* T, const long long* o
     return cudaGetLastError();
 }
 
+// Training target of row i: log2(1 + nnz(C(i,:))) from the row pointers of
+// the exact symbolic phase.
+__global__ void sizer_targets_kernel(const int64_t* __restrict__ rp, long long m,
+                                     float* __restrict__ T) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        T[i] = log2f(1.f + (float)(rp[i + 1] - rp[i]));
+}
+
+// Byte record of a trained predictor (little-endian): magic, format version,
+// F, hidden width, feature-set id, target id, parameter count, the float32
+// parameters, then a 64-bit FNV-1a hash of everything before it.
+constexpr char kSizerMagic[8] = {'S', 'G', 'S', 'I', 'Z', 'E', 'R', 0};
+constexpr uint32_t kSizerVersion = 1;
+constexpr uint32_t kSizerFeatureSet = 1;  // the six log2(1 + .) row features
+constexpr uint32_t kSizerTarget = 1;      // log2(1 + nnz(C(i,:)))
+constexpr size_t kSizerHeader = 8 + 6 * sizeof(uint32_t);
+
+inline size_t sizer_record_bytes(int F) {
+    return kSizerHeader + sizeof(float) * (size_t)sizer_params(F) + sizeof(uint64_t);
+}
+
+inline uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 }  // namespace sg
 
 extern "C" {
@@ -257,6 +289,106 @@ spgemm_status spgemm_sizer_train(const float* X, const float* T, const int64_t* 
             e = cudaGetLastError();
         }
     }
+    if (e != cudaSuccess) {
+        sg::set_last_error(cudaGetErrorString(e));
+        return SPGEMM_ERR_CUDA;
+    }
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_sizer_targets(const int64_t* rowptrC, int64_t m, float* T, void* stream) {
+    if (m < 0 || (m > 0 && (!rowptrC || !T))) {
+        sg::set_last_error("sizer_targets: bad arguments");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    if (m == 0) return SPGEMM_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>((m + 255) / 256, (long long)sms * 8));
+    sg::count_launches(1);
+    sg::sizer_targets_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(rowptrC, m, T);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        sg::set_last_error(cudaGetErrorString(e));
+        return SPGEMM_ERR_CUDA;
+    }
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_sizer_save(const float* params, int32_t F, void* stream, void* buf,
+                                size_t buf_bytes, size_t* bytes_out) {
+    if (F < 1 || F > 64 || !bytes_out) {
+        sg::set_last_error("sizer_save: bad arguments");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    const size_t need = sg::sizer_record_bytes(F);
+    *bytes_out = need;
+    if (!buf) return SPGEMM_OK;  // size query
+    if (buf_bytes < need || !params) {
+        sg::set_last_error("sizer_save: buffer smaller than the record, or params NULL");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    unsigned char* out = (unsigned char*)buf;
+    const uint32_t head[6] = {sg::kSizerVersion, (uint32_t)F, (uint32_t)sg::kSizerH,
+                              sg::kSizerFeatureSet, sg::kSizerTarget,
+                              (uint32_t)sg::sizer_params(F)};
+    std::memcpy(out, sg::kSizerMagic, 8);
+    std::memcpy(out + 8, head, sizeof(head));
+    const size_t pbytes = sizeof(float) * (size_t)sg::sizer_params(F);
+    cudaError_t e = cudaMemcpyAsync(out + sg::kSizerHeader, params, pbytes, cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        sg::set_last_error(cudaGetErrorString(e));
+        return SPGEMM_ERR_CUDA;
+    }
+    const uint64_t h = sg::fnv1a(out, sg::kSizerHeader + pbytes);
+    std::memcpy(out + sg::kSizerHeader + pbytes, &h, sizeof(h));
+    return SPGEMM_OK;
+}
+
+spgemm_status spgemm_sizer_load(const void* buf, size_t buf_bytes, int32_t F, float* params,
+                                void* stream) {
+    const unsigned char* in = (const unsigned char*)buf;
+    if (!in || F < 1 || F > 64) {
+        sg::set_last_error("sizer_load: bad arguments");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    if (buf_bytes < sg::kSizerHeader || std::memcmp(in, sg::kSizerMagic, 8) != 0) {
+        sg::set_last_error("sizer_load: not a predictor record");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    uint32_t head[6];
+    std::memcpy(head, in + 8, sizeof(head));
+    if (head[0] != sg::kSizerVersion) {
+        sg::set_last_error("sizer_load: unknown record version");
+        return SPGEMM_ERR_NOT_SUPPORTED;
+    }
+    if (head[1] != (uint32_t)F || head[2] != (uint32_t)sg::kSizerH ||
+        head[3] != sg::kSizerFeatureSet || head[4] != sg::kSizerTarget ||
+        head[5] != (uint32_t)sg::sizer_params(F)) {
+        sg::set_last_error("sizer_load: record is for another network, feature set or target");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    const size_t pbytes = sizeof(float) * (size_t)sg::sizer_params(F);
+    if (buf_bytes < sg::sizer_record_bytes(F)) {
+        sg::set_last_error("sizer_load: record truncated");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    uint64_t h = 0;
+    std::memcpy(&h, in + sg::kSizerHeader + pbytes, sizeof(h));
+    if (h != sg::fnv1a(in, sg::kSizerHeader + pbytes)) {
+        sg::set_last_error("sizer_load: record hash mismatch");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    if (!params) {
+        sg::set_last_error("sizer_load: params is NULL");
+        return SPGEMM_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaMemcpyAsync(params, in + sg::kSizerHeader, pbytes, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) {
         sg::set_last_error(cudaGetErrorString(e));
         return SPGEMM_ERR_CUDA;

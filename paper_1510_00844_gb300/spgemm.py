@@ -109,6 +109,9 @@ def _load():
         "spgemm_sizer_grad": (st, [P, P, I64_, I32_, P, P, P, P]),
         "spgemm_sizer_train": (st, [P, P, P, I64_, I32_, P, P, P, P, I32_, I32_, ctypes.c_float, P, P]),
         "spgemm_row_features": (st, [P, P]),
+        "spgemm_sizer_targets": (st, [P, I64_, P, P]),
+        "spgemm_sizer_save": (st, [P, I32_, P, P, S, P]),
+        "spgemm_sizer_load": (st, [P, S, I32_, P, P]),
         "spgemm_learned_multiply": (st, [P, P, P, P, ctypes.c_float, P, P, P, P]),
         "spgemm_transpose": (st, [P, P, P, S, P, P, P]),
         "spgemm_plan_info": (st, [P, P]),
@@ -607,20 +610,49 @@ def row_features(p: Plan) -> torch.Tensor:
     return X
 
 
+def sizer_targets(rowptrC: torch.Tensor, stream=None) -> torch.Tensor:
+    """spgemm_sizer_targets: log2(1 + nnz(C(i,:))) per row."""
+    m = rowptrC.numel() - 1
+    T = torch.empty(max(m, 0), dtype=torch.float32, device=rowptrC.device)
+    _check(_lib.spgemm_sizer_targets(ctypes.c_void_p(rowptrC.data_ptr()), m,
+                                     ctypes.c_void_p(T.data_ptr()) if m > 0 else None,
+                                     _stream(stream)))
+    return T
+
+
 def sizer_training_set(pairs, stream=None):
-    """(features, log2(1 + nnz(C(i,:)))) of every non-empty row of the given
-    products, the targets from the exact symbolic phase."""
+    """(features, targets) of every row with products (first feature
+    log2(1 + flops) > 0) of the given products; the targets come from the
+    exact symbolic phase (spgemm_sizer_targets)."""
     Xs, Ts = [], []
     for A, B in pairs:
         p = plan(A, B, stream=stream)
         X = row_features(p)
         rp, _ = symbolic(p)
-        cnt = (rp[1:] - rp[:-1]).to(torch.float32)
+        T = sizer_targets(rp, stream)
         keep = X[:, 0] > 0
         Xs.append(X[keep])
-        Ts.append(torch.log2(1.0 + cnt[keep]))
+        Ts.append(T[keep])
         p.close()
     return torch.cat(Xs), torch.cat(Ts)
+
+
+def sizer_save(params: torch.Tensor, F: int = SIZER_F, stream=None) -> bytes:
+    """spgemm_sizer_save: the trained predictor as a versioned byte record."""
+    need = ctypes.c_size_t()
+    _check(_lib.spgemm_sizer_save(None, F, None, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(_lib.spgemm_sizer_save(ctypes.c_void_p(params.data_ptr()), F, _stream(stream), buf,
+                                  need.value, ctypes.byref(need)))
+    return buf.raw[: need.value]
+
+
+def sizer_load(record: bytes, F: int = SIZER_F, device="cuda", stream=None) -> torch.Tensor:
+    """spgemm_sizer_load: parameters from a record written by sizer_save."""
+    params = torch.empty(sizer_param_count(F), dtype=torch.float32, device=device)
+    _check(_lib.spgemm_sizer_load(record, len(record), F, ctypes.c_void_p(params.data_ptr()),
+                                  _stream(stream)))
+    return params
 
 
 def learned_multiply(A: DeviceCSR, B: DeviceCSR, params: torch.Tensor, margin: float = 0.25,

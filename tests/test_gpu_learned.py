@@ -191,3 +191,39 @@ def test_learned_with_a_broken_predictor_stays_exact(sg):
     assert stats["overflow_rows"] > 0
     assert bool((Cc.rowptr == P.rowptr).all()) and bool((Cc.col == P.col).all())
     assert bool((Cc.val == P.val).all())
+
+
+def test_sizer_targets_match_row_counts(sg):
+    """spgemm_sizer_targets gives log2(1 + nnz(C(i,:))) of the exact row counts
+    (float32; the oracle's counts are exact integers)."""
+    import torch
+    A = inputs.rmat(10, seed=5)
+    dA = sg.to_device(A)
+    p = sg.plan(dA, dA)
+    rp, _ = sg.symbolic(p)
+    T = sg.sizer_targets(rp).cpu().numpy()
+    R = oracle.spgemm(A, A)
+    cnt = np.diff(np.asarray(R.rowptr)).astype(np.float64)
+    np.testing.assert_allclose(T, np.log2(1.0 + cnt), rtol=2e-7, atol=2e-7)
+
+
+def test_sizer_record_round_trip_gives_identical_learned_output(sg, trained):
+    """A predictor saved to bytes and loaded back (as another process would)
+    has the same parameters bit for bit and gives the same learned product."""
+    import torch
+    rec = sg.sizer_save(trained)
+    assert rec[:7] == b"SGSIZER" and len(rec) == 8 + 24 + 4 * sg.sizer_param_count() + 8
+    loaded = sg.sizer_load(rec)
+    assert torch.equal(loaded.view(torch.int32), trained.view(torch.int32))
+    A = inputs.rmat(11, seed=78)
+    dA = sg.to_device(A)
+    C1, s1 = sg.learned_multiply(dA, dA, trained, margin=0.3)
+    C2, s2 = sg.learned_multiply(dA, dA, loaded, margin=0.3)
+    a, b = sg.compact(C1), sg.compact(C2)
+    assert s1["overflow_rows"] == s2["overflow_rows"]
+    assert torch.equal(a.rowptr, b.rowptr) and torch.equal(a.col, b.col)
+    assert torch.equal(a.val.view(torch.int64), b.val.view(torch.int64))
+    bad = bytearray(rec)
+    bad[40] ^= 1                                       # one flipped parameter bit
+    with pytest.raises(sg.SpgemmError):
+        sg.sizer_load(bytes(bad))

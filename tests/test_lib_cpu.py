@@ -85,3 +85,27 @@ def test_kernels_are_compiled_for_sm103a():
     from paper_1510_00844_gb300 import build
     assert ["-gencode", "arch=compute_103a,code=sm_103a"] == build.ARCH
     assert "-fmad=false" in build.FLAGS
+
+
+def test_sizer_record_checks_need_no_gpu(lib):
+    """spgemm_sizer_save answers its size query and spgemm_sizer_load rejects
+    malformed records before touching the device."""
+    P, S, I32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32
+    lib.spgemm_sizer_save.argtypes = [P, I32, P, P, S, ctypes.POINTER(S)]
+    lib.spgemm_sizer_load.argtypes = [P, S, I32, P, P]
+    lib.spgemm_sizer_param_count.argtypes = [I32]
+    need = S()
+    assert lib.spgemm_sizer_save(None, 6, None, None, 0, ctypes.byref(need)) == 0
+    count = lib.spgemm_sizer_param_count(6)
+    assert need.value == 8 + 24 + 4 * count + 8
+    rec = ctypes.create_string_buffer(b"NOTSIZER" + bytes(need.value - 8))
+    assert lib.spgemm_sizer_load(rec, need.value, 6, None, None) == 1          # wrong magic
+    head = b"SGSIZER\x00" + (2).to_bytes(4, "little") + bytes(need.value - 12)
+    rec = ctypes.create_string_buffer(head)
+    assert lib.spgemm_sizer_load(rec, need.value, 6, None, None) == 7          # other version
+    import struct
+    head = b"SGSIZER\x00" + struct.pack("<6I", 1, 6, 32, 1, 1, count)
+    rec = ctypes.create_string_buffer(head + bytes(4 * count + 8))
+    assert lib.spgemm_sizer_load(rec, need.value - 1, 6, None, None) == 1      # truncated
+    assert lib.spgemm_sizer_load(rec, need.value, 6, None, None) == 1          # hash mismatch
+    assert lib.spgemm_sizer_load(rec, need.value, 7, None, None) == 1          # another F
