@@ -66,7 +66,7 @@ def cols_range(P: Piece, c0: int, c1: int) -> Piece:
 
 def rows_range(P: Piece, r0: int, r1: int) -> Piece:
     m, n, rp, col, val = P
-    a, b = int(rp[r0]), int(rp[r1])
+    a, b = rp[[r0, r1]].tolist()
     return (r1 - r0, n, rp[r0:r1 + 1] - a, col[a:b], None if val is None else val[a:b])
 
 
@@ -91,70 +91,86 @@ def hcat(pieces: List[Piece], offsets: List[int], ncols: int) -> Piece:
     return (m, ncols, rp, cl[order].to(pieces[0][3].dtype), val)
 
 
-def _send_piece(P: Piece, dst: int, tag: int, ops: list):
+def _send_piece(P: Piece, dst: int, tag: int, ops: list, keep: list, comm):
     m, n, rp, col, val = P
-    ops.append(dist.P2POp(dist.isend, rp.contiguous(), dst, tag=tag))
-    ops.append(dist.P2POp(dist.isend, col.contiguous(), dst, tag=tag + 1))
-    if val is not None:
-        ops.append(dist.P2POp(dist.isend, val.contiguous(), dst, tag=tag + 2))
+    for t, a in enumerate((rp, col, val)):
+        if a is not None:
+            a = a.contiguous().to(comm)
+            keep.append(a)
+            ops.append(dist.P2POp(dist.isend, a, dst, tag=tag + t))
 
 
 def _alltoall(pieces: Dict[int, Piece], incoming: Dict[int, Tuple[int, int]], col_dtype,
-              val_dtype, device) -> Dict[int, Piece]:
+              val_dtype, device, comm=None) -> Dict[int, Piece]:
     """pieces[dst] goes to rank dst; incoming[src] = (rows, cols) of the piece
-    rank src sends here.  nnz values travel first."""
+    rank src sends here.  nnz values travel first (read back in one copy);
+    messages go through `comm` (default `device`), results land on `device`."""
     me = dist.get_rank()
-    nnz_out = {d: torch.tensor([int(P[3].numel())], dtype=torch.int64, device=device)
+    comm = device if comm is None else comm
+    nnz_out = {d: torch.tensor([int(P[3].numel())], dtype=torch.int64, device=comm)
                for d, P in pieces.items() if d != me}
-    nnz_in = {s: torch.zeros(1, dtype=torch.int64, device=device) for s in incoming if s != me}
+    srcs = [s for s in incoming if s != me]
+    nnz_in = torch.zeros(max(len(srcs), 1), dtype=torch.int64, device=comm)
     ops = [dist.P2POp(dist.isend, t, d, tag=7) for d, t in nnz_out.items()]
-    ops += [dist.P2POp(dist.irecv, t, s, tag=7) for s, t in nnz_in.items()]
+    ops += [dist.P2POp(dist.irecv, nnz_in[t:t + 1], s, tag=7) for t, s in enumerate(srcs)]
     for w in (dist.batch_isend_irecv(ops) if ops else []):
         w.wait()
-    out: Dict[int, Piece] = {}
+    sizes = dict(zip(srcs, nnz_in.tolist()))
+    got: Dict[int, Piece] = {}
     ops = []
+    keep = []
     for s, (m, n) in incoming.items():
         if s == me:
-            out[s] = pieces[me]
             continue
-        k = int(nnz_in[s].item())
-        rp = torch.empty(m + 1, dtype=torch.int64, device=device)
-        cl = torch.empty(k, dtype=col_dtype, device=device)
-        vl = None if val_dtype is None else torch.empty(k, dtype=val_dtype, device=device)
-        out[s] = (m, n, rp, cl, vl)
+        k = sizes[s]
+        rp = torch.empty(m + 1, dtype=torch.int64, device=comm)
+        cl = torch.empty(k, dtype=col_dtype, device=comm)
+        vl = None if val_dtype is None else torch.empty(k, dtype=val_dtype, device=comm)
+        got[s] = (m, n, rp, cl, vl)
         ops.append(dist.P2POp(dist.irecv, rp, s, tag=10))
         ops.append(dist.P2POp(dist.irecv, cl, s, tag=11))
         if vl is not None:
             ops.append(dist.P2POp(dist.irecv, vl, s, tag=12))
     for d, P in pieces.items():
         if d != me:
-            _send_piece(P, d, 10, ops)
+            _send_piece(P, d, 10, ops, keep, comm)
     for w in (dist.batch_isend_irecv(ops) if ops else []):
         w.wait()
+    out: Dict[int, Piece] = {}
+    for s in incoming:
+        if s == me:
+            out[s] = pieces[me]
+        else:
+            m, n, rp, cl, vl = got[s]
+            out[s] = (m, n, rp.to(device), cl.to(device), None if vl is None else vl.to(device))
     return out
 
 
-def _broadcast(P: Optional[Piece], root: int, group, col_dtype, val_dtype, device) -> Piece:
-    """The root's piece on every member of the group."""
+def _broadcast(P: Optional[Piece], root: int, group, col_dtype, val_dtype, device,
+               comm=None) -> Piece:
+    """The root's piece on every member of the group (sent through `comm`,
+    default `device`; returned on `device`)."""
     me = dist.get_rank()
-    hdr = torch.zeros(3, dtype=torch.int64, device=device)
+    comm = device if comm is None else comm
+    hdr = torch.zeros(3, dtype=torch.int64, device=comm)
     if me == root:
         hdr[0], hdr[1], hdr[2] = P[0], P[1], P[3].numel()
     dist.broadcast(hdr, root, group=group)
     m, n, k = (int(x) for x in hdr.tolist())
     if me == root:
-        rp, cl, vl = P[2].contiguous(), P[3].contiguous(), P[4]
+        rp, cl = P[2].contiguous().to(comm), P[3].contiguous().to(comm)
+        vl = None if P[4] is None else P[4].contiguous().to(comm)
     else:
-        rp = torch.empty(m + 1, dtype=torch.int64, device=device)
-        cl = torch.empty(k, dtype=col_dtype, device=device)
-        vl = None if val_dtype is None else torch.empty(k, dtype=val_dtype, device=device)
+        rp = torch.empty(m + 1, dtype=torch.int64, device=comm)
+        cl = torch.empty(k, dtype=col_dtype, device=comm)
+        vl = None if val_dtype is None else torch.empty(k, dtype=val_dtype, device=comm)
     dist.broadcast(rp, root, group=group)
     dist.broadcast(cl, root, group=group)
     if vl is not None:
-        if me == root:
-            vl = vl.contiguous()
         dist.broadcast(vl, root, group=group)
-    return (m, n, rp, cl, vl)
+    if me == root:
+        return P
+    return (m, n, rp.to(device), cl.to(device), None if vl is None else vl.to(device))
 
 
 class Grid:
@@ -178,9 +194,13 @@ class Grid:
 
 def split3d(grid: Grid, A_ijk: Piece, B_ijk: Piece, dims: Tuple[int, int, int],
             multiply: Callable[[Piece, Piece], Piece],
-            merge: Callable[[List[Piece]], Piece], col_dtype, val_dtype, device) -> Piece:
+            merge: Callable[[List[Piece]], Piece], col_dtype, val_dtype, device,
+            comm_device=None) -> Piece:
     """Alg. 2 on this process: returns C_ijk (rows block(m, q, i), columns
-    sub(n, q, c, j, k), local indices)."""
+    sub(n, q, c, j, k), local indices).  Pieces live on `device`; messages go
+    through `comm_device` (default `device`: the GPU under NCCL; the CPU
+    under gloo)."""
+    comm = comm_device
     q, c, i, j, k = grid.q, grid.c, grid.i, grid.j, grid.k
     m, l, n = dims
     # 1. B^ across the fiber: layer k' gets rows sub-block k' of B's row block i
@@ -193,7 +213,7 @@ def split3d(grid: Grid, A_ijk: Piece, B_ijk: Piece, dims: Tuple[int, int, int],
         s0, s1 = sub(n, q, c, j, kk)
         mine0, mine1 = sub(l, q, c, i, k)
         incoming[rank_of(i, j, kk, q, c)] = (mine1 - mine0, s1 - s0)
-    got = _alltoall(pieces, incoming, col_dtype, val_dtype, device)
+    got = _alltoall(pieces, incoming, col_dtype, val_dtype, device, comm)
     j0, j1 = block(n, q, j)
     B_hat = hcat([got[rank_of(i, j, kk, q, c)] for kk in range(c)],
                  [sub(n, q, c, j, kk)[0] - j0 for kk in range(c)], j1 - j0)
@@ -201,9 +221,9 @@ def split3d(grid: Grid, A_ijk: Piece, B_ijk: Piece, dims: Tuple[int, int, int],
     partials = []
     for r in range(q):
         A_rem = _broadcast(A_ijk if j == r else None, rank_of(i, r, k, q, c), grid.row[(i, k)],
-                           col_dtype, val_dtype, device)
+                           col_dtype, val_dtype, device, comm)
         B_rem = _broadcast(B_hat if i == r else None, rank_of(r, j, k, q, c), grid.col[(j, k)],
-                           col_dtype, val_dtype, device)
+                           col_dtype, val_dtype, device, comm)
         partials.append(multiply(A_rem, B_rem))
     # 3. C^int across the fiber: layer k' gets the columns of its sub-block
     i0, i1 = block(m, q, i)
@@ -220,7 +240,7 @@ def split3d(grid: Grid, A_ijk: Piece, B_ijk: Piece, dims: Tuple[int, int, int],
         send = {d: ps[t] for d, ps in pieces.items()}
         s0, s1 = sub(n, q, c, j, k)
         inc = {rank_of(i, j, kk, q, c): (i1 - i0, s1 - s0) for kk in range(c)}
-        got = _alltoall(send, inc, col_dtype, val_dtype, device)
+        got = _alltoall(send, inc, col_dtype, val_dtype, device, comm)
         received += [got[rank_of(i, j, kk, q, c)] for kk in range(c)]
     # 4. local merge (partials in ascending stage, then layer)
     order = [received[t * c + kk] for t in range(q) for kk in range(c)]
