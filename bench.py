@@ -241,6 +241,8 @@ def run_ours(args):
            if rank == 0 and not args.no_e2e else None)
     torch.cuda.empty_cache()
     paths = run_paths(args, A, dA, sg, torch) if (rank == 0 and world == 1 and not args.no_paths) else None
+    if paths is not None:
+        paths["er16384_f64"] = run_config_er16384(sg, torch)
     if paths is not None and not args.no_learned:
         paths["learned"] = run_learned(args, sg, torch)
     cpu = run_cpu_baseline(A) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -336,13 +338,30 @@ def run_paths(args, A, dA, sg, torch):
     same = (nnz == sum(C.nnz for C in ref)
             and bool((colC[:nnz] == torch.cat([C.col for C in ref])).all())
             and bool((valC[:nnz] == torch.cat([C.val for C in ref])).all()))
-    del ref, graph, dp, rowptrC, colC, valC
+    # the same device-sized plan as one persistent chain launch
+    colC.fill_(-1)
+    chain = sg.Chain([(dp, rowptrC, int(bflops), colC, valC)])
+    with torch.cuda.stream(gs):
+        chain.launch(gs)
+    chain.check(gs)
+    tpc = _timed(torch, lambda: chain.launch(gs), reps)
+    chain.check(gs)
+    same_chain = (int(rowptrC[-1].item()) == nnz
+                  and bool((colC[:nnz] == torch.cat([C.col for C in ref])).all())
+                  and bool((valC[:nnz] == torch.cat([C.val for C in ref])).all()))
+    f32_error = batch_f32_error(sg, torch, pairs, ref)
+    del ref, graph, dp, rowptrC, colC, valC, chain
     out["batched_er512_f32"] = {"batched_ms": round(tb * 1e3, 3), "sequential_ms": round(ts * 1e3, 3),
                                 "speedup": round(ts / tb, 3), "flops": int(bflops),
                                 "gflops_batched": round(2 * bflops / tb / 1e9, 3),
                                 "graph_ms": round(tgb * 1e3, 3),
                                 "graph_speedup_vs_sequential": round(ts / tgb, 3),
                                 "graph_bit_identical": bool(same),
+                                "persistent_ms": round(tpc * 1e3, 3),
+                                "persistent_launches": 1,
+                                "persistent_bit_identical": bool(same_chain),
+                                "persistent_speedup_vs_sequential": round(ts / tpc, 3),
+                                "f32_error": f32_error,
                                 "autotune": _tuning_report(best, table)}
     del As, Bs, pairs
     N = 128
@@ -355,6 +374,23 @@ def run_paths(args, A, dA, sg, torch):
     chain.capture()
     tg = _timed(torch, chain.replay, 5)
     chain.check()
+    # the six products of the hierarchy in one persistent launch (the
+    # transposes R_l^T depend only on the given R_l and are formed once)
+    pchain = amg.GalerkinChain(dA0, dRs, s, persistent=True)
+    pchain.capture()
+    pchain.replay()
+    torch.cuda.synchronize()
+    pchain.check()
+    tpg = _timed(torch, pchain.replay, 5)
+    pchain.check()
+    same_p = all(bool(torch.equal(C.col, D.col)) and bool(torch.equal(C.val, D.val))
+                 for C, D in zip(pchain.results(), chain.results()))
+    tr_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(tr_graph, stream=s):
+        for lv in chain.levels:
+            chain._transpose(lv)
+    ttr = _timed(torch, tr_graph.replay, 5)
+    del pchain, tr_graph
 
     def plain_chain():
         A_ = dA0
@@ -376,6 +412,16 @@ def run_paths(args, A, dA, sg, torch):
     out["amg_galerkin_128cubed_3levels"] = {"graph_ms": round(tg * 1e3, 3), "plain_ms": round(tp * 1e3, 3),
                                             "speedup": round(tp / tg, 3), "flops": int(gflops),
                                             "gflops_graph": round(2 * gflops / tg / 1e9, 3),
+                                            "persistent_ms": round(tpg * 1e3, 3),
+                                            "persistent_launches": 1,
+                                            "persistent_bit_identical": bool(same_p),
+                                            "transposes_ms": round(ttr * 1e3, 3),
+                                            "note": "graph_ms: transposes and both products of "
+                                                    "every level as one captured graph of "
+                                                    "library launches; persistent_ms: the six "
+                                                    "products in one persistent launch (a graph "
+                                                    "of a memset and the kernel), transposes "
+                                                    "(transposes_ms) formed once beforehand",
                                             "autotune": _tuning_report(best, table)}
     return out
 
@@ -535,28 +581,46 @@ def run_e2e(args, A, sg, torch, dev, dP):
     h2d = hr.numel() * 8 + hc.numel() * hc.element_size() + hv.numel() * 8
     d2h = 0
     nsteps = max(1, min(args.steps, 2))
+    splits = []
     for it in range(1 + nsteps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         dr.copy_(hr, non_blocking=True)
         dc.copy_(hc, non_blocking=True)
         dv.copy_(hv, non_blocking=True)
+        e1.record()
         M = sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)
-        out_host = pipeline.spgemm_to_host(M, M, panels=8, out=out_host)
+        tm = {}
+        out_host = pipeline.spgemm_to_host(M, M, panels=8, out=out_host, timing=tm)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        tm["h2d_ms"] = e0.elapsed_time(e1)
+        tm["wall_ms"] = (t1 - t0) * 1e3
         nnz = out_host.nnz
         d2h = (A.nrows + 1) * 8 + nnz * (out_host.col.element_size() + 8)
         if it > 0:
             times.append(t1 - t0)
+            splits.append(tm)
         del M
     fl = sg.plan(sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv),
                  sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)).info()["flops"]
     sec = float(np.mean(times))
+    last = splits[-1]
+    split = {k: round(float(np.mean([t[k] for t in splits])), 3)
+             for k in ("h2d_ms", "plans_symbolic_ms", "numeric_ms", "copy_ms", "copy_tail_ms",
+                       "first_numeric_to_last_copy_ms", "wall_ms")}
+    split["h2d_gbs"] = round(h2d / (split["h2d_ms"] * 1e-3) / 1e9, 1)
+    split["d2h_gbs"] = round(last["d2h_bytes"] / (split["copy_ms"] * 1e-3) / 1e9, 1)
     return {"value": round(2.0 * fl / sec / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": round(sec * 1e3, 3), "steps": nsteps,
-            "note": "8 row panels, copies overlapped with the next panel's numeric phase"}
+            "ms_per_step": round(sec * 1e3, 3), "steps": nsteps, "split": split,
+            "note": "8 row panels, copies overlapped with the next panel's numeric phase; "
+                    "split: CUDA-event times of the H2D copy, plans + symbolic phases, "
+                    "numeric phases, device-to-host copies and the copy tail after the "
+                    "last numeric phase"}
 
 
 def oracle_sample(A, target_flops):
@@ -576,7 +640,7 @@ def oracle_sample(A, target_flops):
     return sub, int(fl[rows].sum()), len(rows)
 
 
-def run_cpu_baseline(A, target_flops=3e9, reps=1):
+def run_cpu_baseline(A, target_flops=3e9, reps=1, one_thread_flops=3e8):
     import oracle
     sub, sflops, nrows = oracle_sample(A, target_flops)
     threads = len(os.sched_getaffinity(0))
@@ -588,10 +652,89 @@ def run_cpu_baseline(A, target_flops=3e9, reps=1):
         oracle.spgemm(sub, A, nthreads=threads)
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
+    sub1, sflops1, nrows1 = oracle_sample(A, one_thread_flops)
+    t0 = time.perf_counter()
+    oracle.spgemm(sub1, A, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": round(2.0 * sflops / best / 1e9, 4), "unit": UNIT,
             "cores": oracle.num_threads(threads), "kind": "oracle",
             "sample": f"{nrows} seeded random rows of A (flops {sflops}) times A; "
-                      f"{best:.2f} s wall"}
+                      f"{best:.2f} s wall",
+            "one_thread": {"value": round(2.0 * sflops1 / dt1 / 1e9, 4), "unit": UNIT,
+                           "sample": f"{nrows1} seeded random rows (flops {sflops1}); "
+                                     f"{dt1:.2f} s wall"}}
+
+
+def run_config_er16384(sg, torch):
+    """The small configuration: C = A.A, A Erdos-Renyi n = 16384 with exactly
+    8 nonzeros per column, float64.  GPU: the plain two-phase path (plan,
+    symbolic, numeric), CUDA events, best of 10 after 3 warm-ups.  Oracle:
+    the whole product on all host cores and on one core (best of 3), with
+    the GPU result compared to it entry by entry."""
+    import oracle
+    from paper_1510_00844_gb300 import inputs
+    A = inputs.er_column_regular(16384, 8, inputs.BASE_SEED + 1)
+    dA = sg.to_device(A)
+    s = torch.cuda.current_stream()
+    best = None
+    for it in range(13):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        C = sg.spgemm(dA, dA)
+        e1.record(s)
+        torch.cuda.synchronize()
+        if it >= 3:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    flops = int(sg.plan(dA, dA).info()["flops"])
+    threads = len(os.sched_getaffinity(0))
+    times = {}
+    for nt in (threads, 1):
+        bt = None
+        for _ in range(3):
+            t0 = time.perf_counter()
+            R = oracle.spgemm(A, A, nthreads=nt)
+            dt = time.perf_counter() - t0
+            bt = dt if bt is None else min(bt, dt)
+        times[nt] = bt
+    rp, col, val = C.to_host()
+    same = (np.array_equal(rp, R.rowptr) and np.array_equal(col.astype(np.int64), R.col)
+            and bool(np.all(np.abs(val - R.val) <= 1e-12 * np.abs(R.val))))
+    return {"flops": flops, "nnz_C": int(C.nnz), "gpu_ms": round(best, 4),
+            "gpu_gflops": round(2 * flops / (best * 1e-3) / 1e9, 3),
+            "oracle_s": round(times[threads], 4), "oracle_cores": oracle.num_threads(threads),
+            "oracle_1thread_s": round(times[1], 4), "matches_oracle": bool(same),
+            "note": "plan + symbolic + numeric on the GPU; the whole product on the host"}
+
+
+def batch_f32_error(sg, torch, pairs, Cs, sample=24):
+    """Error of float32 accumulation against the float64 oracle on a seeded
+    sample of the batched products: per entry |c32 - c64| / sum_k |a||b|,
+    its maximum, and its maximum relative to gamma_q = q u / (1 - q u)
+    (u = 2^-24, q = the entry's number of terms), the recursive-summation
+    bound the tests assert."""
+    import oracle
+    from paper_1510_00844_gb300 import inputs
+    rng = np.random.default_rng(17)
+    pick = rng.choice(len(pairs), min(sample, len(pairs)), replace=False)
+    u = 2.0 ** -24
+    worst, worst_ratio, entries = 0.0, 0.0, 0
+    for q in pick:
+        a, b = pairs[q]
+        a64 = inputs.CSR(a.nrows, a.ncols, a.rowptr, a.col, a.val.astype(np.float64))
+        b64 = inputs.CSR(b.nrows, b.ncols, b.rowptr, b.col, b.val.astype(np.float64))
+        R = oracle.spgemm(a64, b64)
+        S = oracle.spgemm(a64.with_values(np.abs(a64.val)), b64.with_values(np.abs(b64.val)))
+        Q = oracle.spgemm(a64.with_values(np.ones(a.nnz)), b64.with_values(np.ones(b.nnz)))
+        c32 = Cs[q].val.cpu().numpy().astype(np.float64)
+        err = np.abs(c32 - R.val) / np.where(S.val > 0, S.val, 1.0)
+        gq = Q.val * u / (1 - Q.val * u)
+        worst = max(worst, float(err.max(initial=0.0)))
+        worst_ratio = max(worst_ratio, float((err / gq).max(initial=0.0)))
+        entries += int(R.nnz)
+    return {"products_sampled": int(len(pick)), "entries": entries,
+            "max_err_over_sum_abs": worst, "max_err_over_gamma_q": round(worst_ratio, 4),
+            "u": u}
 
 
 def run_reference(args):

@@ -197,6 +197,62 @@ spgemm_status spgemm_plan_device(int32_t count, const spgemm_csr* A, const spgem
 spgemm_status spgemm_execute(spgemm_plan_t plan, void* ws, size_t ws_bytes, int64_t* rowptrC,
                              int64_t capacity, void* colC, void* valC);
 
+/* ---- persistent chains (not in the paper: batching and dependent chains of
+ * products in one launch; the paper's nearest point is that R^T A and
+ * (R^T A) R carry too little work for large concurrency, Sec. 5.4) ----
+ * A chain is an ordered list of device-sized products (spgemm_plan_device).
+ * spgemm_chain_launch runs all of them, every phase of every product, in ONE
+ * persistent kernel launch: a resident grid that waits at a device-side
+ * barrier after each phase (analysis, binning, symbolic, two scan stages,
+ * numeric), so a product may read the output of an earlier product of the
+ * chain (its A or B arrays may be that product's rowptrC/colC/valC, with nnz
+ * fields read as capacities, as for spgemm_plan_device).  Results are the same
+ * bit for bit as spgemm_execute on each plan in turn.  Each step gives its
+ * plan, the plan's workspace (spgemm_workspace_size), and its outputs as for
+ * spgemm_execute.  All steps use one index type and one value type (float64,
+ * float32, int64 or Boolean; NOT_SUPPORTED otherwise).
+ * Every barrier wait is bounded by opts.timeout_s (0: 10 s): a wait that
+ * expires sets the chain's status, every block of the grid returns, and
+ * spgemm_chain_check reports SPGEMM_ERR_TIMEOUT (outputs undefined).
+ * opts.withhold_stage >= 0 makes no block signal the end of that stage (a
+ * test of the timeout path); -1 otherwise.  Per-product errors (capacity,
+ * rows too wide) are read with spgemm_check on each plan. */
+typedef struct {
+    spgemm_plan_t plan;     /* from spgemm_plan_device */
+    void* ws;               /* the plan's workspace */
+    size_t ws_bytes;
+    int64_t* rowptrC;       /* int64[R + 1] */
+    int64_t capacity;       /* entries of colC / valC */
+    void* colC;
+    void* valC;             /* NULL for Boolean products */
+} spgemm_chain_step;
+
+typedef struct {
+    double timeout_s;       /* bound of every barrier wait; 0 = 10 s */
+    int32_t withhold_stage; /* -1, or a stage whose completion is withheld (tests) */
+    int32_t reserved;
+} spgemm_chain_opts;
+
+typedef struct spgemm_chain_s* spgemm_chain_t;
+
+/* Device bytes of a chain's workspace (step table and barrier state). */
+size_t spgemm_chain_workspace_size(int32_t nsteps);
+/* Checks the steps and uploads the step table into chain_ws (caller-owned,
+ * 256-byte aligned, kept until the chain is destroyed); waits for the upload.
+ * The library keeps only the host handle. */
+spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps,
+                                  const spgemm_chain_opts* opts, void* chain_ws,
+                                  size_t chain_ws_bytes, spgemm_chain_t* chain);
+/* Enqueues the whole chain on `stream`: one memset of the barrier state and
+ * one kernel launch; no host readback, so it can be captured in a CUDA
+ * graph.  Does not wait. */
+spgemm_status spgemm_chain_launch(spgemm_chain_t chain, void* stream);
+/* Waits for `stream` and reads the chain's status: OK or TIMEOUT. */
+spgemm_status spgemm_chain_check(spgemm_chain_t chain, void* stream);
+/* Blocks of the last launch's grid (0 before the first launch). */
+int32_t spgemm_chain_grid(spgemm_chain_t chain);
+void spgemm_chain_destroy(spgemm_chain_t chain);
+
 /* ---- learned sizing of C (not in the paper: an addition to the method) ----
  * A small MLP predicts nnz(C(i,:)) from row features: x = log2(1 + .) of
  * flops_i, |A(i,:)|, max_k |B(k,:)|, n, flops_i / |A(i,:)|, min(flops_i, n);

@@ -1,5 +1,5 @@
 """Galerkin hierarchy A_{l+1} = R_l^T A_l R_l on the GPU, all levels in one
-CUDA graph.
+CUDA graph, or in one persistent kernel launch.
 
 The paper multiplies a matrix by its restriction operator to coarsen it
 (Sec. 5.4: R^T A, then (R^T A) R).  Here every level's transpose and both
@@ -19,9 +19,17 @@ from . import spgemm as sg
 
 
 class GalerkinChain:
+    """persistent=False: every level's transpose and both products as
+    device-sized library calls (about 140 launches, captured in one graph).
+    persistent=True: the transposes R_l^T (which depend only on the given
+    R_l) are formed once here, and the six products run as one persistent
+    chain launch (spgemm_chain_launch): a graph of two nodes."""
+
     def __init__(self, A0: sg.DeviceCSR, Rs: List[sg.DeviceCSR], stream: torch.cuda.Stream,
-                 max_row_nnz: int = 64, tuning: Optional[sg.Tuning] = None):
+                 max_row_nnz: int = 64, tuning: Optional[sg.Tuning] = None,
+                 persistent: bool = False, timeout_s: float = 0.0):
         self.stream = stream
+        self.persistent = persistent
         self.Rs = Rs
         dev = A0.rowptr.device
         cap = A0.nnz
@@ -49,15 +57,32 @@ class GalerkinChain:
             self.levels.append(dict(R=R, cR=cR, tws=tws, Rt=Rt, T=T, A=An, p1=p1, p2=p2, cap=cap))
             A = An
         self.graph = None
+        self.chain = None
+        if persistent:
+            with torch.cuda.stream(stream):
+                for lv in self.levels:
+                    self._transpose(lv)
+            stream.synchronize()
+            steps = []
+            for lv in self.levels:
+                steps.append((lv["p1"], lv["T"].rowptr, lv["cap"], lv["T"].col, lv["T"].val))
+                steps.append((lv["p2"], lv["A"].rowptr, lv["cap"], lv["A"].col, lv["A"].val))
+            self.chain = sg.Chain(steps, timeout_s=timeout_s)
+
+    def _transpose(self, lv):
+        Rt = lv["Rt"]
+        sg._check(sg._lib.spgemm_transpose(
+            ctypes.byref(lv["cR"]), sg._stream(self.stream),
+            ctypes.c_void_p(lv["tws"].data_ptr()), lv["tws"].numel(),
+            ctypes.c_void_p(Rt.rowptr.data_ptr()), ctypes.c_void_p(Rt.col.data_ptr()),
+            ctypes.c_void_p(Rt.val.data_ptr())))
 
     def _enqueue(self):
+        if self.chain is not None:
+            self.chain.launch(self.stream)
+            return
         for lv in self.levels:
-            R, Rt = lv["R"], lv["Rt"]
-            sg._check(sg._lib.spgemm_transpose(
-                ctypes.byref(lv["cR"]), sg._stream(self.stream),
-                ctypes.c_void_p(lv["tws"].data_ptr()), lv["tws"].numel(),
-                ctypes.c_void_p(Rt.rowptr.data_ptr()), ctypes.c_void_p(Rt.col.data_ptr()),
-                ctypes.c_void_p(Rt.val.data_ptr())))
+            self._transpose(lv)
             sg.execute(lv["p1"], lv["T"].rowptr, lv["cap"], lv["T"].col, lv["T"].val)
             sg.execute(lv["p2"], lv["A"].rowptr, lv["cap"], lv["A"].col, lv["A"].val)
 
@@ -76,6 +101,8 @@ class GalerkinChain:
         self.graph.replay()
 
     def check(self):
+        if self.chain is not None:
+            self.chain.check(self.stream)
         for lv in self.levels:
             sg.check(lv["p1"])
             sg.check(lv["p2"])

@@ -116,6 +116,8 @@ WsLayout workspace_layout(const Plan& P) {
     if (dense) off += align_up((size_t)P.seg_total * sizeof(int32_t));
     L.runlen = off;
     if (dense) off += align_up((size_t)P.run_total * sizeof(int32_t));
+    L.nextrun = off;
+    if (dense) off += align_up((size_t)P.run_total * sizeof(int2));
     L.arena = off;
     L.arena_stride = std::max<long long>(1, P.max_dense_len);
     if (dense)

@@ -1,0 +1,58 @@
+// Types of the persistent chain executor (see chain.cuh for the kernel):
+// the per-product table the kernel walks, its barrier state, and the
+// launcher templates instantiated in inst_chain_*.cu.
+#pragma once
+
+#include "plan.h"
+
+namespace sg {
+
+constexpr int kChainThreads = 256;   // 8 warps per persistent block
+constexpr int kChainWarps = kChainThreads / 32;
+constexpr int kDevTimeout = 8;       // a chain barrier wait expired
+
+// One product of a chain: everything its stages read, from a device-sized
+// plan, its workspace and its output arrays.
+struct ChainProduct {
+    const ProdDesc* D;
+    const long long* rb;
+    const long long* bb;
+    DevCounters* cnt;
+    int64_t* flops;
+    unsigned char* cls;
+    int32_t* rows;
+    int64_t* cap;
+    const float* prm;
+    int32_t* chunkcnt;
+    int32_t* segtab;
+    int32_t* runlen;
+    int2* nextrun;
+    DenseCursor* arena;
+    int64_t* scan;        // tile sums of the row-pointer scan
+    int64_t* rowptrC;
+    void* colC;
+    void* valC;
+    long long R, LB, max_dense_n, arena_stride, capacity;
+    float margin;
+    int nprod, W, dense_min, hash_shift, seg_log2, max_words;
+};
+
+// Barrier state (first 16 bytes cleared by the host before every launch)
+// and the chain's configuration.
+struct ChainSync {
+    unsigned int arrived;   // barrier arrivals of this launch
+    int status;             // kDevOk or kDevTimeout
+    int abort;
+    int pad0;
+    unsigned long long timeout_ns;
+    int withhold;           // stage whose completion no block signals (-1: none)
+    int nsteps;
+};
+
+template <class IT, class V>
+size_t chain_smem_bytes(int max_words);
+template <class IT, class V>
+cudaError_t launch_chain(const ChainProduct* steps, ChainSync* sync, int max_words, int sm_count,
+                         cudaStream_t s, int* grid_out);
+
+}  // namespace sg

@@ -1,0 +1,8 @@
+// Persistent chain kernels, int64_t column indices, double and float values (one
+// unit per pair, so that they compile in parallel with the other units).
+#include "chain_launch.h"
+
+namespace sg {
+SG_INSTANTIATE_CHAIN(int64_t, double)
+SG_INSTANTIATE_CHAIN(int64_t, float)
+}  // namespace sg

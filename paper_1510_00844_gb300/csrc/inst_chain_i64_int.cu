@@ -1,0 +1,8 @@
+// Persistent chain kernels, int64_t column indices, int64_t and NoVal values (one
+// unit per pair, so that they compile in parallel with the other units).
+#include "chain_launch.h"
+
+namespace sg {
+SG_INSTANTIATE_CHAIN(int64_t, int64_t)
+SG_INSTANTIATE_CHAIN(int64_t, NoVal)
+}  // namespace sg

@@ -179,12 +179,13 @@ __device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* r
 constexpr int kSizerF = 6;
 
 template <class IT>
-__global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
+__device__ __forceinline__ void analyze_kernel_body(long long R, const ProdDesc* __restrict__ D,
                                const long long* __restrict__ rb, int nprod, long long max_dense_n,
                                int dense_min, int64_t* __restrict__ flops_out,
                                unsigned char* __restrict__ cls_out, DevCounters* cnt,
                                const float* __restrict__ prm, float margin,
-                               int64_t* __restrict__ cap_out, int hash_shift) {
+                               int64_t* __restrict__ cap_out, int hash_shift,
+        const long long vbid, const long long vnb) {
     __shared__ unsigned long long hist[kNumClasses];
     __shared__ unsigned long long blk_total, blk_max, blk_dlen;
     __shared__ int blk_unsup;
@@ -201,8 +202,8 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
     }
     __syncthreads();
     const int lane = lane_id();
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = ((long long)vbid * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)vnb * blockDim.x) >> 5;
     unsigned long long my_total = 0, my_max = 0;
     for (long long r = warp; r < R; r += nwarps) {
         const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
@@ -275,6 +276,17 @@ __global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
     }
 }
 
+template <class IT>
+__global__ void analyze_kernel(long long R, const ProdDesc* __restrict__ D,
+                               const long long* __restrict__ rb, int nprod, long long max_dense_n,
+                               int dense_min, int64_t* __restrict__ flops_out,
+                               unsigned char* __restrict__ cls_out, DevCounters* cnt,
+                               const float* __restrict__ prm, float margin,
+                               int64_t* __restrict__ cap_out, int hash_shift) {
+    analyze_kernel_body<IT>(R, D, rb, nprod, max_dense_n, dense_min, flops_out, cls_out, cnt,
+        prm, margin, cap_out, hash_shift, (long long)blockIdx.x, (long long)gridDim.x);
+}
+
 // Features of every global row for the row-size predictor (log2(1 + .) of
 // flops, |A(i,:)|, max_k |B(k,:)|, n, flops/|A(i,:)|, min(flops, n)).
 template <class IT>
@@ -334,10 +346,11 @@ __global__ void validate_kernel(long long m, long long ncols, long long nnz, con
 // --------------------------------------------------- symbolic: hash rows
 // One warp per row; table of 2^LOG2T keys per warp.  Row count -> rowcnt[i].
 template <class IT, int LOG2T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-    symbolic_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+__device__ __forceinline__ void symbolic_hash_kernel_body(
+    const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
                          int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
-                         int cls, int64_t* __restrict__ rowcnt, int* err) {
+                         int cls, int64_t* __restrict__ rowcnt, int* err,
+        const long long vbid, const long long vnb) {
     using K = typename KeyT<IT>::type;
     constexpr int T = 1 << LOG2T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -348,8 +361,8 @@ __global__ void __launch_bounds__(WARPS * 32)
     __syncwarp();
     const long long nrows = (long long)cnt->class_count[cls];
     const int32_t* crow = rows + cnt->class_off[cls];
-    const long long gw = (long long)blockIdx.x * WARPS + w;
-    const long long nw = (long long)gridDim.x * WARPS;
+    const long long gw = (long long)vbid * WARPS + w;
+    const long long nw = (long long)vnb * WARPS;
     for (long long rr = gw; rr < nrows; rr += nw) {
         const long long r = crow[rr];
         const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
@@ -386,6 +399,15 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+template <class IT, int LOG2T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    symbolic_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
+                         int cls, int64_t* __restrict__ rowcnt, int* err) {
+    symbolic_hash_kernel_body<IT, LOG2T, WARPS>(D, rb, nprod, rows, cnt, cls, rowcnt, err,
+        (long long)blockIdx.x, (long long)gridDim.x);
+}
+
 // -------------------------------------------------- symbolic: dense rows
 // One block per row (dynamic row grabbing), bitmap of the product's n columns
 // in shared memory (sized for the largest n of the batch).  Also writes the
@@ -395,12 +417,13 @@ __global__ void __launch_bounds__(WARPS * 32)
 // six 256-thread or three 512-thread blocks share an SM, or one 1024-thread
 // block for a bitmap that leaves room for only one block).
 template <class IT, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+__device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __restrict__ D,
                                       const long long* __restrict__ rb, int nprod,
                                       const int32_t* __restrict__ rows, const DevCounters* cnt,
                                       int max_words, int chunk_words,
                                       int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
-                                      unsigned long long* work, int* err) {
+                                      unsigned long long* work, int* err,
+        const long long vbid, const long long vnb) {
     extern __shared__ unsigned bm[];
     __shared__ long long row_total;
     __shared__ long long cur_row;
@@ -473,6 +496,17 @@ __global__ void __launch_bounds__(MAXT, MINB) symbolic_dense_kernel(const ProdDe
         }
         __syncthreads();
     }
+}
+
+template <class IT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) symbolic_dense_kernel(const ProdDesc* __restrict__ D,
+                                      const long long* __restrict__ rb, int nprod,
+                                      const int32_t* __restrict__ rows, const DevCounters* cnt,
+                                      int max_words, int chunk_words,
+                                      int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
+                                      unsigned long long* work, int* err) {
+    symbolic_dense_kernel_body<IT, MAXT, MINB>(D, rb, nprod, rows, cnt, max_words, chunk_words,
+        chunkcnt, rowcnt, work, err, (long long)blockIdx.x, (long long)gridDim.x);
 }
 
 // ---------------------------------------------------- numeric: hash rows
@@ -564,13 +598,14 @@ __device__ __forceinline__ bool warp_radix_sort(K* k0, V* v0, K* k1, V* v1, int 
 // One warp per row; table of 2^LOG2T (key, value) slots; products added in
 // ascending k (ordered rounds); table compacted, sorted, written.
 template <class IT, class V, int LOG2T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-    numeric_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+__device__ __forceinline__ void numeric_hash_kernel_body(
+    const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
                         int cls, const int64_t* __restrict__ rpC, long long cap,
                         IT* __restrict__ ciC, V* __restrict__ vC, int* err,
                         int64_t* __restrict__ rowend, int32_t* __restrict__ overflow,
-                        unsigned* overflow_count) {
+                        unsigned* overflow_count,
+        const long long vbid, const long long vnb) {
     using K = typename KeyT<IT>::type;
     constexpr int T = 1 << LOG2T;
     constexpr bool HV = VOps<V>::has_val;
@@ -597,8 +632,8 @@ __global__ void __launch_bounds__(WARPS * 32)
     __syncwarp();
     const long long nrows = (long long)cnt->class_count[cls];
     const int32_t* crow = rows + cnt->class_off[cls];
-    const long long gw = (long long)blockIdx.x * WARPS + w;
-    const long long nw = (long long)gridDim.x * WARPS;
+    const long long gw = (long long)vbid * WARPS + w;
+    const long long nw = (long long)vnb * WARPS;
     for (long long rr = gw; rr < nrows; rr += nw) {
         const long long r = crow[rr];
         const RowCtx<IT, V> c = row_ctx<IT, V>(D, rb, nprod, r);
@@ -826,6 +861,18 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+template <class IT, class V, int LOG2T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    numeric_hash_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                        int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
+                        int cls, const int64_t* __restrict__ rpC, long long cap,
+                        IT* __restrict__ ciC, V* __restrict__ vC, int* err,
+                        int64_t* __restrict__ rowend, int32_t* __restrict__ overflow,
+                        unsigned* overflow_count) {
+    numeric_hash_kernel_body<IT, V, LOG2T, WARPS>(D, rb, nprod, rows, cnt, cls, rpC, cap, ciC,
+        vC, err, rowend, overflow, overflow_count, (long long)blockIdx.x, (long long)gridDim.x);
+}
+
 // --------------------------------------------------- numeric: dense rows
 // Work units: a dense row's P column chunks (width W) are cut into G equal
 // segments (G in {1, 2, 4, ..., kSegGrid}, chosen per flops class so that a
@@ -843,12 +890,12 @@ __host__ __device__ __forceinline__ long long seg_chunk(int g, int P) {
 }
 
 // Where a warp stands in B(k,:) while it sweeps the chunks of a row: the
-// position, the entries left in the row, and the column at the position
-// (INT_MAX when none), so a chunk with nothing of B(k,:) costs one load.
+// first unconsumed position, its column (INT_MAX once B(k,:) is used up) and
+// its run length (entries from pos to the end of that column's chunk).
 struct __align__(16) DenseCursor {
     long long pos;
-    int left;
-    int next_col;
+    int col;
+    int rl;
 };
 
 // One run of a batch in the dense numeric kernel: the flattened product f
@@ -861,22 +908,29 @@ struct __align__(16) DenseRun {
 
 // runlen[run_base + q] = number of entries from q to the end of q's column
 // chunk (col / W) inside its row of B: the length of the part of B(k,:) that
-// a chunk sweep consumes in one step.  One warp per B row of every product,
-// windows of 32 from the row end backwards.
+// a chunk sweep consumes in one step.  nextrun[run_base + q] = {length, first
+// column} of the run that follows the one starting at q ({0, INT_MAX} at the
+// row's end), so a cursor advances with one load whose address it knows
+// before the chunk's products are accumulated.  One warp per B row of every
+// product: run lengths in windows of 32 from the row end backwards, then the
+// successor table in a forward pass over what the warp wrote.
 template <class IT>
-__global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
+__device__ __forceinline__ void runlen_kernel_body(long long LB, const ProdDesc* __restrict__ D,
                               const long long* __restrict__ bb, int nprod, int W,
-                              int32_t* __restrict__ runlen, const DevCounters* cnt) {
+                              int32_t* __restrict__ runlen, int2* __restrict__ nextrun,
+                              const DevCounters* cnt,
+        const long long vbid, const long long vnb) {
     if (cnt->class_off[kNumClasses] == cnt->class_off[kClassDense0]) return;  // no dense rows
     const int lane = lane_id();
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = ((long long)vbid * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)vnb * blockDim.x) >> 5;
     for (long long kb = warp; kb < LB; kb += nwarps) {
         const int pr = nprod > 1 ? find_prod(bb, nprod, kb) : 0;
         const ProdDesc& d = D[pr];
         const long long k = kb - d.brow_base;
         const IT* ciB = (const IT*)d.ciB;
         int32_t* rl = runlen + d.run_base;
+        int2* nr = nextrun + d.run_base;
         const long long s0 = d.rpB[k], s1 = d.rpB[k + 1];
         long long carry_end = s1;          // run end of the window after this one
         long long carry_chunk = -1;        // chunk of the first entry of that window
@@ -898,19 +952,37 @@ __global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
             carry_end = __shfl_sync(kFull, end, 0);
             carry_chunk = __shfl_sync(kFull, ch, 0);
         }
+        __syncwarp();   // the run lengths of the whole row are visible to the warp
+        for (long long q = s0 + lane; q < s1; q += 32) {
+            const long long q2 = q + rl[q];
+            int2 x = make_int2(0, 0x7fffffff);
+            if (q2 < s1) x = make_int2(rl[q2], (int)ciB[q2]);
+            nr[q] = x;
+        }
+        __syncwarp();
     }
+}
+
+template <class IT>
+__global__ void runlen_kernel(long long LB, const ProdDesc* __restrict__ D,
+                              const long long* __restrict__ bb, int nprod, int W,
+                              int32_t* __restrict__ runlen, int2* __restrict__ nextrun,
+                              const DevCounters* cnt) {
+    runlen_kernel_body<IT>(LB, D, bb, nprod, W, runlen, nextrun, cnt, (long long)blockIdx.x,
+        (long long)gridDim.x);
 }
 
 // segtab[seg_base + k * (kSegGrid+1) + g] = first position p in B(k,:) with
 // col >= seg_chunk(g, P) * W, relative to rowptr[k].
 template <class IT>
-__global__ void segtab_kernel(long long LB, const ProdDesc* __restrict__ D,
+__device__ __forceinline__ void segtab_kernel_body(long long LB, const ProdDesc* __restrict__ D,
                               const long long* __restrict__ bb, int nprod, int W,
-                              int32_t* __restrict__ segtab, const DevCounters* cnt) {
+                              int32_t* __restrict__ segtab, const DevCounters* cnt,
+        const long long vbid, const long long vnb) {
     if (cnt->class_off[kNumClasses] == cnt->class_off[kClassDense0]) return;  // no dense rows
     const long long total = LB * (kSegGrid + 1);
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = (long long)vbid * blockDim.x + threadIdx.x; t < total;
+         t += (long long)vnb * blockDim.x) {
         const long long kb = t / (kSegGrid + 1);
         const int g = (int)(t - kb * (kSegGrid + 1));
         const int pr = nprod > 1 ? find_prod(bb, nprod, kb) : 0;
@@ -929,18 +1001,109 @@ __global__ void segtab_kernel(long long LB, const ProdDesc* __restrict__ D,
     }
 }
 
+template <class IT>
+__global__ void segtab_kernel(long long LB, const ProdDesc* __restrict__ D,
+                              const long long* __restrict__ bb, int nprod, int W,
+                              int32_t* __restrict__ segtab, const DevCounters* cnt) {
+    segtab_kernel_body<IT>(LB, D, bb, nprod, W, segtab, cnt, (long long)blockIdx.x,
+        (long long)gridDim.x);
+}
+
+// Products of one batch of (up to 32) A entries inside the chunk starting at
+// column c0: lane e holds entry e's run (here, its B position pos, length len
+// and a = A(i,k)).  The runs are flattened into rounds of 32 products in
+// ascending k, four rounds per step so that their loads overlap; a round's
+// products are multiplied and added in k order (lanes of one round that hit
+// the same slot add in lane order, i.e. in ascending k).
+template <class IT, class V>
+__device__ __forceinline__ void dense_batch(bool here, long long pos, int len, V a, long long c0,
+                                            const IT* __restrict__ ciB, const V* __restrict__ vB,
+                                            V* acc, unsigned* bm, DenseRun<V>* runs) {
+    const unsigned hmask = __ballot_sync(kFull, here);
+    const int mylen = here ? len : 0;
+    const int incl = warp_incl_scan(mylen);
+    const int excl = incl - mylen;
+    const int total = __shfl_sync(kFull, incl, 31);
+    // nonempty runs in k order: run e starts at flattened position excl_e, its
+    // products are B[off_e + f] for f in the run
+    if (here) {
+        DenseRun<V> re;
+        re.off = pos - excl;
+        re.a = a;
+        runs[__popc(hmask & lanemask_lt())] = re;
+    }
+    __syncwarp();
+    // The run of lane x in the round starting at w0 is (runs started before
+    // w0) + (runs starting in [w0, w0 + x]) - 1, from an OR of start bits.
+    int started = 0;
+    for (int f0 = 0; f0 < total; f0 += 128) {
+        const int nsub = min(4, (total - f0 + 31) >> 5);
+        long long jj[4];
+        V bv[4];
+        V av[4];
+        bool vl[4];
+        bool multi[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            vl[t] = false;
+            multi[t] = false;
+            jj[t] = c0;
+            bv[t] = V{};
+            av[t] = V{};
+            if (t < nsub) {
+                const int w0 = f0 + 32 * t;
+                const unsigned sbit =
+                    (here && excl >= w0 && excl < w0 + 32) ? (1u << (excl - w0)) : 0u;
+                const unsigned M = __reduce_or_sync(kFull, sbit);
+                const int e = started + __popc(M & lanemask_le()) - 1;
+                started += __popc(M);
+                multi[t] = (M & ~1u) != 0u;
+                const int fi = w0 + lane_id();
+                vl[t] = fi < total;
+                if (vl[t]) {
+                    const DenseRun<V> re = runs[e];
+                    const long long q = re.off + fi;
+                    jj[t] = (long long)ciB[q];
+                    bv[t] = load_val(vB, q);
+                    av[t] = re.a;
+                }
+            }
+        }
+        V v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v[t] = V{};
+            if (t < nsub && vl[t]) v[t] = VOps<V>::mul(av[t], bv[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (t < nsub) {
+                const int slot = (int)(jj[t] - c0);
+                if (vl[t]) atomicOr(&bm[slot >> 5], 1u << (slot & 31));
+                if (multi[t]) ordered_add(acc, slot, vl[t], v[t]);
+                else plain_add(acc, slot, vl[t], v[t]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// The register cap (three 8-warp or six 4-warp blocks per SM) keeps 24
+// warps resident, which the shared-memory accumulators allow.
 template <class IT, class V, int W, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-    numeric_dense_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+__device__ __forceinline__ void numeric_dense_kernel_body(
+    const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
                          int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
                          const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
-                         const int32_t* __restrict__ runlen, DenseCursor* __restrict__ arena,
-                         long long arena_stride, const int64_t* __restrict__ rpC, long long cap,
-                         IT* __restrict__ ciC, V* __restrict__ vC, long long max_dense_n,
-                         unsigned long long* work, int* err, int64_t* __restrict__ rowend,
-                         int32_t* __restrict__ overflow, unsigned* overflow_count,
-                         int64_t* __restrict__ unit_cnt) {
+                         const int32_t* __restrict__ runlen, const int2* __restrict__ nextrun,
+                         DenseCursor* __restrict__ arena, long long arena_stride,
+                         const int64_t* __restrict__ rpC, long long cap, IT* __restrict__ ciC,
+                         V* __restrict__ vC, long long max_dense_n, unsigned long long* work,
+                         int* err, int64_t* __restrict__ rowend, int32_t* __restrict__ overflow,
+                         unsigned* overflow_count, int64_t* __restrict__ unit_cnt,
+        const long long vbid, const long long vnb) {
     constexpr bool HV = VOps<V>::has_val;
+    constexpr int kNone = 0x7fffffff;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
@@ -949,7 +1112,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     V* acc = reinterpret_cast<V*>(base);
     unsigned* bm = reinterpret_cast<unsigned*>(base + vbytes);
     DenseRun<V>* runs = reinterpret_cast<DenseRun<V>*>(base + vbytes + W / 8);
-    DenseCursor* cursor = arena + ((long long)blockIdx.x * WARPS + w) * arena_stride;
+    DenseCursor* cursor = arena + ((long long)vbid * WARPS + w) * arena_stride;
     for (int s = lane; s < W; s += 32)
         if constexpr (HV) acc[s] = VOps<V>::init();
     for (int s = lane; s < W / 32; s += 32) bm[s] = 0u;
@@ -991,6 +1154,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int32_t* ccnt = chunkcnt + cx.chunk_base + cx.i * P;
         const int32_t* stab = segtab + cx.seg_base;
         const int32_t* rlen = runlen + cx.run_base;
+        const int2* nrun = nextrun + cx.run_base;
         // Slot mode (learned sizing, no symbolic pass): the row's predicted
         // slot [rpC[r], rpC[r+1]) is split over its segments in proportion
         // to their chunks; a segment that outgrows its share lists the row
@@ -1018,115 +1182,53 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
         }
         const long long out_begin = out;
-        // cursors at the segment start; the smallest next column over all
-        // cursors names the next chunk with any product, so chunks without
-        // products are jumped over
-        int min_next = 0x7fffffff;
+        // cursors at the segment start; the smallest column over all cursors
+        // names the next chunk with any product, so chunks without products
+        // are jumped over
+        int min_next = kNone;
         for (long long p = a0 + lane; p < a1; p += 32) {
-            long long k = (long long)ciA[p];
-            long long s0 = rpB[k];
-            long long s1 = rpB[k + 1];
-            long long c0p = g0 == 0 ? s0 : s0 + stab[k * (kSegGrid + 1) + g0];
+            const long long k = (long long)ciA[p];
+            const long long s1 = rpB[k + 1];
+            const long long c0p = g0 == 0 ? rpB[k] : rpB[k] + stab[k * (kSegGrid + 1) + g0];
             DenseCursor nc;
             nc.pos = c0p;
-            nc.left = (int)(s1 - c0p);
-            nc.next_col = nc.left > 0 ? (int)ciB[c0p] : 0x7fffffff;
+            nc.col = c0p < s1 ? (int)ciB[c0p] : kNone;
+            nc.rl = c0p < s1 ? rlen[c0p] : 0;
             cursor[p - a0] = nc;
-            min_next = min(min_next, nc.next_col);
+            min_next = min(min_next, nc.col);
         }
         min_next = warp_min(min_next);
         __syncwarp();
         for (int c = max(cs, min_next / W); c < ce;) {
             const long long c0 = (long long)c * W;
             const long long c1 = min(c0 + (long long)W, n);
-            int cnext = 0x7fffffff;  // smallest next column after this chunk
+            int cnext = kNone;  // smallest column after this chunk
+            // batches of 32 entries: cursors and A values are loaded together
+            // (neither address depends on the other); a cursor's next run is
+            // loaded before the batch is accumulated and used after it
             for (long long bb = a0; bb < a1; bb += 32) {
-                const int nb = (int)min(32LL, a1 - bb);
                 const long long p = bb + lane;
-                DenseCursor cs2{0, 0, 0x7fffffff};
-                if (lane < nb) cs2 = cursor[p - a0];
-                const bool here = lane < nb && (long long)cs2.next_col < c1;
-                if (!here) cnext = min(cnext, cs2.next_col);
-                const unsigned hmask = __ballot_sync(kFull, here);
-                if (hmask == 0u) continue;
-                // the part of B(k,:) inside this chunk: runlen entries from the cursor
-                int len = 0;
+                DenseCursor cur{0, kNone, 0};
                 V a = VOps<V>::init();
-                if (here) {
-                    len = rlen[cs2.pos];
+                if (p < a1) {
+                    cur = cursor[p - a0];
                     a = load_val(vA, p);
                 }
-                const int incl = warp_incl_scan(len);
-                const int excl = incl - len;
-                const int total = __shfl_sync(kFull, incl, 31);
-                // nonempty runs in k order: run e starts at flattened position
-                // excl_e, its products are B[off_e + f] for f in the run
-                if (here) {
-                    DenseRun<V> re;
-                    re.off = cs2.pos - excl;
-                    re.a = a;
-                    runs[__popc(hmask & lanemask_lt())] = re;
-                }
-                __syncwarp();
-                // flattened rounds of 32 products in ascending k; up to four
-                // rounds per step so their loads overlap.  The run of lane x in
-                // the round starting at w0 is (runs started before w0) + (runs
-                // starting in [w0, w0 + x]) - 1, from an OR of start bits.
-                int started = 0;
-                for (int f0 = 0; f0 < total; f0 += 128) {
-                    const int nsub = min(4, (total - f0 + 31) >> 5);
-                    long long jj[4];
-                    V bv[4];
-                    V av[4];
-                    bool vl[4];
-                    bool multi[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if (t < nsub) {
-                            const int w0 = f0 + 32 * t;
-                            const unsigned sbit =
-                                (here && excl >= w0 && excl < w0 + 32) ? (1u << (excl - w0)) : 0u;
-                            const unsigned M = __reduce_or_sync(kFull, sbit);
-                            const int e = started + __popc(M & lanemask_le()) - 1;
-                            started += __popc(M);
-                            multi[t] = (M & ~1u) != 0u;
-                            const int fi = w0 + lane;
-                            vl[t] = fi < total;
-                            jj[t] = c0;
-                            bv[t] = V{};
-                            av[t] = V{};
-                            if (vl[t]) {
-                                const DenseRun<V> re = runs[e];
-                                const long long q = re.off + fi;
-                                jj[t] = (long long)ciB[q];
-                                bv[t] = load_val(vB, q);
-                                av[t] = re.a;
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if (t < nsub) {
-                            const int slot = (int)(jj[t] - c0);
-                            V v{};
-                            if (vl[t]) {
-                                atomicOr(&bm[slot >> 5], 1u << (slot & 31));
-                                v = VOps<V>::mul(av[t], bv[t]);
-                            }
-                            if (multi[t]) ordered_add(acc, slot, vl[t], v);
-                            else plain_add(acc, slot, vl[t], v);
-                        }
-                    }
-                }
+                const bool here = p < a1 && (long long)cur.col < c1;
+                int2 nx = make_int2(0, kNone);
+                if (here) nx = nrun[cur.pos];
+                if (__any_sync(kFull, here))
+                    dense_batch<IT, V>(here, cur.pos, cur.rl, a, c0, ciB, vB, acc, bm, runs);
                 if (here) {
                     DenseCursor nc;
-                    nc.pos = cs2.pos + len;
-                    nc.left = cs2.left - len;
-                    nc.next_col = nc.left > 0 ? (int)ciB[nc.pos] : 0x7fffffff;
+                    nc.pos = cur.pos + cur.rl;
+                    nc.col = nx.y;
+                    nc.rl = nx.x;
                     cursor[p - a0] = nc;
-                    cnext = min(cnext, nc.next_col);
+                    cnext = min(cnext, nc.col);
+                } else {
+                    cnext = min(cnext, cur.col);
                 }
-                __syncwarp();
             }
             // emit the chunk in column order: lane t owns bitmap word t (32
             // columns), a warp scan of the popcounts gives each lane its output
@@ -1167,6 +1269,22 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
         }
     }
+}
+
+template <class IT, class V, int W, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS)
+    numeric_dense_kernel(const ProdDesc* __restrict__ D, const long long* __restrict__ rb,
+                         int nprod, const int32_t* __restrict__ rows, const DevCounters* cnt,
+                         const int32_t* __restrict__ chunkcnt, const int32_t* __restrict__ segtab,
+                         const int32_t* __restrict__ runlen, const int2* __restrict__ nextrun,
+                         DenseCursor* __restrict__ arena, long long arena_stride,
+                         const int64_t* __restrict__ rpC, long long cap, IT* __restrict__ ciC,
+                         V* __restrict__ vC, long long max_dense_n, unsigned long long* work,
+                         int* err, int64_t* __restrict__ rowend, int32_t* __restrict__ overflow,
+                         unsigned* overflow_count, int64_t* __restrict__ unit_cnt) {
+    numeric_dense_kernel_body<IT, V, W, WARPS>(D, rb, nprod, rows, cnt, chunkcnt, segtab, runlen,
+        nextrun, arena, arena_stride, rpC, cap, ciC, vC, max_dense_n, work, err, rowend,
+        overflow, overflow_count, unit_cnt, (long long)blockIdx.x, (long long)gridDim.x);
 }
 
 // Learned sizing: close the gaps a slot-mode dense row leaves between its

@@ -107,8 +107,8 @@ cudaError_t sym_hash_bin(Plan& P, int bin, int64_t* rowcnt) {
     return cudaGetLastError();
 }
 
-// Tables of B the dense numeric kernel walks with: segment starts per B row
-// and the run length of every B entry inside its chunk.
+// Tables of B the dense numeric kernel walks with: segment starts per B row,
+// the run length of every B entry inside its chunk and each run's successor.
 template <class IT>
 cudaError_t launch_dense_tables(Plan& P, unsigned char* ws) {
     WsLayout L = workspace_layout(P);
@@ -124,7 +124,8 @@ cudaError_t launch_dense_tables(Plan& P, unsigned char* ws) {
         long long g2 = grid_for(P.LB, 8, P.sm_count, 8);
         count_launches(1);
         runlen_kernel<IT><<<(unsigned)g2, 256, 0, P.stream>>>(P.LB, P.d_descs, P.bb, P.nprod, P.W,
-                                                              (int32_t*)(ws + L.runlen), P.cnt);
+                                                              (int32_t*)(ws + L.runlen),
+                                                              (int2*)(ws + L.nextrun), P.cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return e;
@@ -215,7 +216,7 @@ cudaError_t launch_numeric_dense(Plan& P, unsigned char* ws, const int64_t* rpC,
     k<<<(unsigned)P.dense_grid, WARPS * 32, smem, P.stream>>>(
         P.d_descs, P.rb, P.nprod, P.rows, P.cnt, (const int32_t*)(ws + L.chunkcnt),
         (const int32_t*)(ws + L.segtab), (const int32_t*)(ws + L.runlen),
-        (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, P.max_dense_n, work,
+        (const int2*)(ws + L.nextrun), (DenseCursor*)(ws + L.arena), L.arena_stride, rpC, cap, colC, valC, P.max_dense_n, work,
         &P.cnt->err, rowend, overflow, overflow_count, P.unit_cnt);
     return cudaGetLastError();
 }

@@ -91,7 +91,7 @@ void count_launches(long long k);
 void set_last_error(const char* msg);
 
 struct WsLayout {
-    size_t chunkcnt = 0, segtab = 0, runlen = 0, arena = 0, scan = 0, total = 0;
+    size_t chunkcnt = 0, segtab = 0, runlen = 0, nextrun = 0, arena = 0, scan = 0, total = 0;
     long long arena_stride = 0;
 };
 WsLayout workspace_layout(const Plan& P);

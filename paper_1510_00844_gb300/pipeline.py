@@ -42,10 +42,18 @@ def host_buffers(nrows: int, nnz: int, col_dtype, val_dtype) -> HostCSR:
 
 def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIMES,
                    panels: int = 8, copy_streams: int = 2, out: Optional[HostCSR] = None,
-                   tuning: Optional[sg.Tuning] = None) -> HostCSR:
+                   tuning: Optional[sg.Tuning] = None, timing: Optional[dict] = None) -> HostCSR:
     """C = A.B into pinned host memory (see the module docstring).  `out`
-    is reused when it is large enough; otherwise new buffers are pinned."""
+    is reused when it is large enough; otherwise new buffers are pinned.
+    With `timing` (a dict), CUDA events record where the time goes; the
+    dict receives milliseconds for the plans and symbolic phases, the
+    numeric phases, the copies, the copy tail after the last numeric phase,
+    and the bytes copied to the host."""
     dev = A.rowptr.device
+    ev_t0 = None
+    if timing is not None:
+        ev_t0 = torch.cuda.Event(enable_timing=True)
+        ev_t0.record(torch.cuda.current_stream(dev))
     m = A.nrows
     panels = max(1, min(int(panels), max(m, 1)))
     bounds = [((m * p) // panels, (m * (p + 1)) // panels) for p in range(panels)]
@@ -61,6 +69,10 @@ def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIM
         plans.append(p)
         rowptrs.append(rp)
         counts.append(int(nnz))
+    ev_sym = None
+    if timing is not None:
+        ev_sym = torch.cuda.Event(enable_timing=True)
+        ev_sym.record(compute)
     offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     total = int(offs[-1])
     pattern = plans[0].pattern_only
@@ -77,12 +89,20 @@ def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIM
                      None if pattern else torch.empty(max(cap, 1), dtype=val_dtype, device=dev)))
     copiers = [torch.cuda.Stream(dev) for _ in range(max(1, copy_streams))]
     free = [None] * len(bufs)            # event: the buffer's last copy finished
+    num_ev, copy_ev = [], []
     for p, (a, b) in enumerate(bounds):
         k = p % len(bufs)
         colb, valb = bufs[k]
         if free[k] is not None:
             compute.wait_event(free[k])
+        if timing is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(compute)
         sg.numeric(plans[p], rowptrs[p], colb, valb)
+        if timing is not None:
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(compute)
+            num_ev.append((e0, e1))
         rp_glob = rowptrs[p][1:] + int(offs[p])
         ready = torch.cuda.Event()
         ready.record(compute)
@@ -92,6 +112,9 @@ def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIM
         for j, s in enumerate(copiers):
             s.wait_event(ready)
             lo, hi = (n * j) // len(copiers), (n * (j + 1)) // len(copiers)
+            if timing is not None and j == 0:
+                c0 = torch.cuda.Event(enable_timing=True)
+                c0.record(s)
             with torch.cuda.stream(s):
                 if hi > lo:
                     out.col[o + lo:o + hi].copy_(colb[lo:hi], non_blocking=True)
@@ -104,13 +127,25 @@ def spgemm_to_host(A: sg.DeviceCSR, B: sg.DeviceCSR, semiring: int = sg.PLUS_TIM
                 done.append(ev)
         for ev in done[1:]:
             copiers[0].wait_event(ev)
-        fin = torch.cuda.Event()
+        fin = torch.cuda.Event(enable_timing=timing is not None)
         fin.record(copiers[0])
         free[k] = fin
+        if timing is not None:
+            copy_ev.append((c0, fin))
         rp_glob.record_stream(copiers[0])
     out.rowptr[0] = 0
     for s in copiers:
         s.synchronize()
+    if timing is not None:
+        compute.synchronize()
+        timing["plans_symbolic_ms"] = ev_t0.elapsed_time(ev_sym)
+        timing["numeric_ms"] = sum(x.elapsed_time(y) for x, y in num_ev)
+        timing["copy_ms"] = sum(x.elapsed_time(y) for x, y in copy_ev)
+        timing["copy_tail_ms"] = num_ev[-1][1].elapsed_time(copy_ev[-1][1]) if num_ev else 0.0
+        timing["first_numeric_to_last_copy_ms"] = (num_ev[0][0].elapsed_time(copy_ev[-1][1])
+                                                   if num_ev else 0.0)
+        elem = col_dtype.itemsize + (0 if val_dtype is None else val_dtype.itemsize)
+        timing["d2h_bytes"] = int(total) * elem + (m + 1) * 8
     for p in plans:
         p.close()
     return out

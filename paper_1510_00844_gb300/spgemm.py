@@ -126,6 +126,12 @@ def _load():
         "spgemm_merge_numeric": (st, [I32_, P, P, P, P, S, P, P, P]),
         "spgemm_merge_check": (st, [P, P]),
         "spgemm_merge_symbolic_static": (st, [I32_, P, P, P, P, P]),
+        "spgemm_chain_workspace_size": (S, [I32_]),
+        "spgemm_chain_create": (st, [I32_, P, P, P, S, P]),
+        "spgemm_chain_launch": (st, [P, P]),
+        "spgemm_chain_check": (st, [P, P]),
+        "spgemm_chain_grid": (I32_, [P]),
+        "spgemm_chain_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -322,6 +328,63 @@ def execute(p: BatchPlan, rowptrC: torch.Tensor, capacity: int, colC: torch.Tens
                                ctypes.c_void_p(colC.data_ptr()) if colC.numel() else None,
                                None if valC is None or valC.numel() == 0
                                else ctypes.c_void_p(valC.data_ptr())))
+
+
+class _ChainStep(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("rowptrC", ctypes.c_void_p), ("capacity", ctypes.c_int64),
+                ("colC", ctypes.c_void_p), ("valC", ctypes.c_void_p)]
+
+
+class _ChainOpts(ctypes.Structure):
+    _fields_ = [("timeout_s", ctypes.c_double), ("withhold_stage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Chain:
+    """spgemm_chain_*: device-sized products run in ONE persistent kernel
+    launch.  steps: (plan from device_plan, rowptrC, capacity, colC, valC); a
+    step may read an earlier step's outputs.  launch() enqueues (capturable
+    in a CUDA graph), check() waits and raises SpgemmError(TIMEOUT) when a
+    barrier wait expired."""
+
+    def __init__(self, steps, timeout_s: float = 0.0, withhold_stage: int = -1):
+        self._steps = list(steps)
+        dev = self._steps[0][1].device
+        arr = (_ChainStep * len(self._steps))()
+        for t, (p, rp, cap, col, val) in enumerate(self._steps):
+            arr[t] = _ChainStep(p._h.value, p.ws.data_ptr(), p.ws.numel(), rp.data_ptr(), int(cap),
+                                col.data_ptr() if col is not None and col.numel() else None,
+                                None if val is None or val.numel() == 0 else val.data_ptr())
+        self.ws = _workspace(_lib.spgemm_chain_workspace_size(len(self._steps)), dev)
+        opts = _ChainOpts(float(timeout_s), int(withhold_stage), 0)
+        h = ctypes.c_void_p()
+        _check(_lib.spgemm_chain_create(len(self._steps), arr, ctypes.byref(opts),
+                                        ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                        ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.spgemm_chain_launch(self._h, _stream(stream)))
+
+    def check(self, stream=None):
+        _check(_lib.spgemm_chain_check(self._h, _stream(stream)))
+        for p, *_ in self._steps:
+            check(p)
+
+    def grid(self) -> int:
+        return int(_lib.spgemm_chain_grid(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.spgemm_chain_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def batch_rowptrs(p: BatchPlan, rowptrC: torch.Tensor) -> torch.Tensor:
