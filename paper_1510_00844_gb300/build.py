@@ -31,16 +31,6 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-# The persistent chain kernel reads, after a grid barrier, data that other
-# SMs wrote earlier in the same launch; its units load global memory through
-# L2 (no L1 allocation), which keeps those reads coherent.
-PER_UNIT_FLAGS = {"inst_chain_": ["-Xptxas", "-dlcm=cg"]}
-
-
-def _unit_flags(src):
-    name = os.path.basename(src)
-    return [f for key, fl in PER_UNIT_FLAGS.items() if name.startswith(key) for f in fl]
-
 
 def _deps():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu*")) + glob.glob(os.path.join(CSRC, "*.h"))
@@ -64,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc] + ARCH + flags + _unit_flags(src) + ["-c", src, "-o", obj]
+        cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -122,7 +122,8 @@ spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps
         max_words = std::max(max_words, (std::min(P->max_n, P->max_dense_n) + 31) / 32);
         // the dense stages use 8 warps per persistent block; their cursor
         // arena slots must exist in the plan's workspace
-        if (P->dense_grid * P->dense_warps_per_block < (long long)P->sm_count * sg::kChainWarps)
+        const int dense_warps = P->W == sg::kDenseW0 ? sg::kChainWarps : sg::kChainHalf;
+        if (P->dense_grid * P->dense_warps_per_block < (long long)P->sm_count * dense_warps)
             return chain_fail(SPGEMM_ERR_NOT_SUPPORTED, "plan's dense arena too small for a chain");
     }
     // the dense symbolic bitmap shares the persistent block's shared memory

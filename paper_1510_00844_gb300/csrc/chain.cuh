@@ -220,8 +220,10 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         symbolic_hash_kernel_body<IT, 10, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
                                                        kClassHash0 + 2, c.rowptrC, err, bid, nb);
         __syncthreads();
-        symbolic_hash_kernel_body<IT, 11, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                       kClassHash0 + 3, c.rowptrC, err, bid, nb);
+        if (threadIdx.x < kChainHalf * 32)
+            symbolic_hash_kernel_body<IT, 11, kChainHalf>(c.D, c.rb, c.nprod, c.rows, c.cnt,
+                                                          kClassHash0 + 3, c.rowptrC, err, bid,
+                                                          nb);
         __syncthreads();
         if (c.LB > 0) {
             segtab_kernel_body<IT>(c.LB, c.D, c.bb, c.nprod, c.W, c.segtab, c.cnt, bid, nb);
@@ -250,13 +252,14 @@ __global__ void __launch_bounds__(kChainThreads, 1)
                                                         colC, valC, err, nullptr, nullptr,
                                                         nullptr, bid, nb);
         __syncthreads();
-        numeric_hash_kernel_body<IT, V, 10, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                         kClassHash0 + 2, c.rowptrC, c.capacity,
-                                                         colC, valC, err, nullptr, nullptr,
-                                                         nullptr, bid, nb);
+        if (threadIdx.x < kChainHalf * 32)
+            numeric_hash_kernel_body<IT, V, 10, kChainHalf>(c.D, c.rb, c.nprod, c.rows, c.cnt,
+                                                            kClassHash0 + 2, c.rowptrC,
+                                                            c.capacity, colC, valC, err, nullptr,
+                                                            nullptr, nullptr, bid, nb);
         __syncthreads();
         // the largest hash bin keeps the 4-warp table layout of its standalone
-        // kernel (its tables fill the shared memory): warps 4..7 wait
+        // kernel (its tables fill the shared memory)
         if (threadIdx.x < 128)
             numeric_hash_kernel_body<IT, V, 11, 4>(c.D, c.rb, c.nprod, c.rows, c.cnt,
                                                    kClassHash0 + 3, c.rowptrC, c.capacity, colC,
@@ -267,8 +270,8 @@ __global__ void __launch_bounds__(kChainThreads, 1)
                 c.D, c.rb, c.nprod, c.rows, c.cnt, c.chunkcnt, c.segtab, c.runlen, c.nextrun,
                 c.arena, c.arena_stride, c.rowptrC, c.capacity, colC, valC, c.max_dense_n,
                 &c.cnt->work_counter[1], err, nullptr, nullptr, nullptr, nullptr, bid, nb);
-        else
-            numeric_dense_kernel_body<IT, V, kDenseW1, kChainWarps>(
+        else if (threadIdx.x < kChainHalf * 32)
+            numeric_dense_kernel_body<IT, V, kDenseW1, kChainHalf>(
                 c.D, c.rb, c.nprod, c.rows, c.cnt, c.chunkcnt, c.segtab, c.runlen, c.nextrun,
                 c.arena, c.arena_stride, c.rowptrC, c.capacity, colC, valC, c.max_dense_n,
                 &c.cnt->work_counter[1], err, nullptr, nullptr, nullptr, nullptr, bid, nb);
@@ -281,10 +284,13 @@ template <class IT, class V>
 size_t chain_smem_bytes(int max_words) {
     using K = typename KeyT<IT>::type;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t b = (size_t)kChainWarps * (1u << 11) * sizeof(K);                       // symbolic bins
-    b = std::max(b, (size_t)kChainWarps * ((1u << 10) * (sizeof(K) + vb) + 1024));  // numeric bin 2
+    size_t b = (size_t)kChainWarps * (1u << 10) * sizeof(K);                      // symbolic bin 2
+    b = std::max(b, (size_t)kChainHalf * (1u << 11) * sizeof(K));                   // symbolic bin 3
+    b = std::max(b, (size_t)kChainWarps * ((1u << 8) * (sizeof(K) + vb) + 1024));   // numeric bin 1
+    b = std::max(b, (size_t)kChainHalf * ((1u << 10) * (sizeof(K) + vb) + 1024));   // numeric bin 2
     b = std::max(b, (size_t)4 * ((1u << 11) * (sizeof(K) + vb) + 1024));            // numeric bin 3
-    b = std::max(b, (size_t)kChainWarps * ((vb * kDenseW1) + kDenseW1 / 8 + 32 * sizeof(DenseRun<V>)));
+    b = std::max(b, (size_t)kChainWarps * ((vb * kDenseW0) + kDenseW0 / 8 + 32 * sizeof(DenseRun<V>)));
+    b = std::max(b, (size_t)kChainHalf * ((vb * kDenseW1) + kDenseW1 / 8 + 32 * sizeof(DenseRun<V>)));
     b = std::max(b, (size_t)max_words * 4);                                         // dense symbolic
     return b;
 }

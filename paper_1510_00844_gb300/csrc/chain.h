@@ -7,8 +7,12 @@
 
 namespace sg {
 
-constexpr int kChainThreads = 256;   // 8 warps per persistent block
+constexpr int kChainThreads = 512;   // 16 warps per persistent block
 constexpr int kChainWarps = kChainThreads / 32;
+// Warps of the persistent block that run a stage whose per-warp shared
+// memory would not fit 16 times (the largest hash bins, wide dense chunks);
+// the other warps wait at the stage's end.
+constexpr int kChainHalf = kChainWarps / 2;
 constexpr int kDevTimeout = 8;       // a chain barrier wait expired
 
 // One product of a chain: everything its stages read, from a device-sized
