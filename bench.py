@@ -539,27 +539,51 @@ def run_learned(args, sg, torch):
     del views, dA, A
     torch.cuda.empty_cache()
     print("learned rmat20:", json.dumps(out), flush=True, file=sys.stderr)
-    if not args.mcl:
+    if args.no_mcl:
         return out
+    out["mcl5_rmat20"] = run_mcl(args, sg, torch, params, margin)
+    return out
+
+
+def run_mcl(args, sg, torch, params, margin):
+    """Five MCL expansions (M^T M^T, prune < 1e-4, renormalise) on a
+    column-stochastic R-MAT scale 20 matrix with learned sizing, per step
+    flops, panels, nnz before and after pruning, product and prune times;
+    the exact two-phase path runs on every `--mcl-compare`-th panel of every
+    step (and on all panels with --mcl), on the same input, with the pruned
+    panels compared bit for bit."""
+    from paper_1510_00844_gb300 import inputs
     M = inputs.mcl_transition(20)
-    dM = sg.to_device(M)
-    res = {}
-    for mode in ("plain", "learned"):
-        X = dM
+    X = sg.to_device(M)
+    every = 1 if args.mcl else max(1, args.mcl_compare)
+    steps = []
+    total_ms = 0.0
+    same = True
+    lt = pt = 0.0
+    for _ in range(5):
+        st = {}
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(5):
-            X = sg.mcl_step(X, 1e-4, params=params if mode == "learned" else None, margin=margin)
+        X = sg.mcl_step(X, 1e-4, params=params, margin=margin, stats=st, compare_every=every)
         torch.cuda.synchronize()
-        res[mode] = (time.perf_counter() - t0, _checksum(torch, X), X.nnz)
-        del X
+        ms = (time.perf_counter() - t0) * 1e3
+        total_ms += ms
+        same = same and st["compared_identical"]
+        lt += st["compared_learned_ms"]
+        pt += st["compared_plain_ms"]
+        steps.append({"flops": st["flops"], "panels": st["panels"],
+                      "nnz_before_prune": st["nnz_product"], "nnz_after_prune": st["nnz_pruned"],
+                      "product_ms": round(st["product_ms"], 1), "prune_ms": round(st["prune_ms"], 1),
+                      "gflops": round(2 * st["flops"] / (st["product_ms"] * 1e-3) / 1e9, 2),
+                      "compared_panels": st["compared_panels"]})
         torch.cuda.empty_cache()
-    out["mcl5_rmat20"] = {"plain_ms": round(res["plain"][0] * 1e3, 1),
-                          "learned_ms": round(res["learned"][0] * 1e3, 1),
-                          "speedup": round(res["plain"][0] / res["learned"][0], 3),
-                          "nnz_final": int(res["plain"][2]),
-                          "bit_identical": res["plain"][1] == res["learned"][1]}
-    return out
+    return {"steps": steps, "learned_step_total_ms": round(total_ms, 1), "nnz_final": int(X.nnz),
+            "compared_every": every, "compared_learned_ms": round(lt, 1),
+            "compared_plain_ms": round(pt, 1), "speedup_on_compared": round(pt / lt, 3) if lt else None,
+            "bit_identical": bool(same),
+            "note": "learned sizing on every panel; the exact two-phase product and prune on the "
+                    "compared panels of each step, same input; wall time of a step includes the "
+                    "compared panels' plain products"}
 
 
 def run_e2e(args, A, sg, torch, dev, dP):
@@ -827,7 +851,10 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-sizing comparison (R-MAT 20 squaring)")
     ap.add_argument("--mcl", action="store_true",
-                    help="add five MCL steps on R-MAT 20 to the learned-sizing leg (about 9 min)")
+                    help="compare the MCL steps against the exact path on every panel (slow)")
+    ap.add_argument("--no-mcl", action="store_true", help="skip the five MCL steps")
+    ap.add_argument("--mcl-compare", type=int, default=16,
+                    help="compare every k-th MCL panel against the exact two-phase path")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the split / batched / AMG comparisons")
     ap.add_argument("--profile-leg", choices=["product", "kslice", "batched", "amg", "mis2"],

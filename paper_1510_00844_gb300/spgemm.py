@@ -575,24 +575,66 @@ def masked_spgemm(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, semiring: int = PLUS
 
 
 def mcl_step(M: DeviceCSR, threshold: float = 1e-4, params: Optional[torch.Tensor] = None,
-             margin: float = 0.25, stream=None, panel_bytes: float = 32e9) -> DeviceCSR:
+             margin: float = 0.25, stream=None, panel_bytes: float = 32e9,
+             stats: Optional[dict] = None, compare_every: int = 0) -> DeviceCSR:
     """One MCL expansion on M^T in CSR: (M M)^T = M^T M^T, then the epilogue.
     With params the product uses learned sizing.  When the unpruned product
     could exceed panel_bytes (flops bound x 12 bytes), rows are processed in
-    panels, each pruned before the next is formed."""
+    panels, each pruned before the next is formed.  With `stats` (a dict),
+    the step records its flops, panels, nnz before and after pruning and the
+    product / prune times (CUDA events, milliseconds).  With params and
+    compare_every = k > 0, every k-th panel is also formed by the exact
+    two-phase product; stats then records both paths' times on those panels
+    and whether their pruned outputs are identical."""
     fl = plan(M, M, stream=stream).info()["flops"]
     npan = max(1, int(np.ceil(fl * (M.col.element_size() + 8) / panel_bytes)))
     parts = []
+    if stats is not None:
+        stats.update(flops=int(fl), panels=npan, nnz_product=0, product_ms=0.0, prune_ms=0.0)
+        if params is not None and compare_every > 0:
+            stats.update(compared_panels=0, compared_identical=True, compared_learned_ms=0.0,
+                         compared_plain_ms=0.0)
+        s_ = torch.cuda.current_stream() if stream is None else stream
     for p in range(npan):
         a, b = (M.nrows * p) // npan, (M.nrows * (p + 1)) // npan
         V = M if npan == 1 else DeviceCSR(b - a, M.ncols, M.rowptr[a:b], M.col, M.val,
                                           rowend=M.rowptr[a + 1:b + 1])
+        if stats is not None:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(s_)
         if params is None:
             C = spgemm(V, M, stream=stream)
         else:
             C, _ = learned_multiply(V, M, params, margin, stream=stream)
+        if stats is not None:
+            ev[1].record(s_)
         parts.append(mcl_prune(C, threshold, stream))
+        if stats is not None:
+            ev[2].record(s_)
+            ev[2].synchronize()
+            stats["product_ms"] += ev[0].elapsed_time(ev[1])
+            stats["prune_ms"] += ev[1].elapsed_time(ev[2])
+            stats["nnz_product"] += int(C.rowend.sum() - C.rowptr[:-1].sum()) \
+                if C.rowend is not None else int(C.nnz)
+            if params is not None and compare_every > 0 and p % compare_every == 0:
+                ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev2[0].record(s_)
+                Cp = spgemm(V, M, stream=stream)
+                Pp = mcl_prune(Cp, threshold, stream)
+                ev2[1].record(s_)
+                ev2[1].synchronize()
+                L = parts[-1]
+                stats["compared_panels"] += 1
+                stats["compared_learned_ms"] += ev[0].elapsed_time(ev[2])
+                stats["compared_plain_ms"] += ev2[0].elapsed_time(ev2[1])
+                stats["compared_identical"] = bool(
+                    stats["compared_identical"] and torch.equal(Pp.rowptr, L.rowptr)
+                    and torch.equal(Pp.col, L.col)
+                    and torch.equal(Pp.val.view(torch.int64), L.val.view(torch.int64)))
+                del Cp, Pp
         del C
+    if stats is not None:
+        stats["nnz_pruned"] = int(sum(P.nnz for P in parts))
     if npan == 1:
         return parts[0]
     offs = np.cumsum([0] + [P.nnz for P in parts])
