@@ -186,6 +186,41 @@ __device__ __forceinline__ void chain_zero_rows(const ChainProduct& c, long long
         c.rowptrC[erow[r]] = 0;
 }
 
+// Warps of the persistent block that run a hash bin with tables of 2^LOG2T
+// slots: all 16 while their tables fit the shared-memory budget, else 8, else
+// 4 (the others wait at the stage's end).
+constexpr size_t kChainSmemBudget = 208 * 1024;
+template <class K, class V, int LOG2T, bool NUMERIC>
+constexpr int chain_bin_warps() {
+    constexpr size_t vb = NUMERIC && VOps<V>::has_val ? sizeof(V) : 0;
+    constexpr size_t per = (size_t(1) << LOG2T) * (sizeof(K) + vb) + (NUMERIC ? 1024 : 0);
+    return 16 * per <= kChainSmemBudget ? 16 : 8 * per <= kChainSmemBudget ? 8 : 4;
+}
+
+// One hash bin of the symbolic / numeric stage on the warps its tables allow.
+template <class IT, class K, int LOG2T>
+__device__ __forceinline__ void chain_sym_bin(const ChainProduct& c, int* err, long long bid,
+                                              long long nb) {
+    constexpr int WARPS = chain_bin_warps<K, NoVal, LOG2T, false>();
+    const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
+    if (threadIdx.x < WARPS * 32)
+        symbolic_hash_kernel_body<IT, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
+                                                    c.rowptrC, err, bid, nb);
+    __syncthreads();
+}
+
+template <class IT, class V, class K, int LOG2T>
+__device__ __forceinline__ void chain_num_bin(const ChainProduct& c, IT* colC, V* valC, int* err,
+                                              long long bid, long long nb) {
+    constexpr int WARPS = chain_bin_warps<K, V, LOG2T, true>();
+    const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
+    if (threadIdx.x < WARPS * 32)
+        numeric_hash_kernel_body<IT, V, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
+                                                      c.rowptrC, c.capacity, colC, valC, err,
+                                                      nullptr, nullptr, nullptr, bid, nb);
+    __syncthreads();
+}
+
 template <class IT, class V>
 __global__ void __launch_bounds__(kChainThreads, 1)
     chain_kernel(const ChainProduct* __restrict__ steps, ChainSync* sync) {
@@ -211,20 +246,11 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         if (!chain_barrier(sync, stage++)) return;
         // symbolic phase: row counts into rowptrC
         chain_zero_rows(c, bid, nb);
-        symbolic_hash_kernel_body<IT, 6, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                      kClassHash0, c.rowptrC, err, bid, nb);
-        __syncthreads();
-        symbolic_hash_kernel_body<IT, 8, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                      kClassHash0 + 1, c.rowptrC, err, bid, nb);
-        __syncthreads();
-        symbolic_hash_kernel_body<IT, 10, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                       kClassHash0 + 2, c.rowptrC, err, bid, nb);
-        __syncthreads();
-        if (threadIdx.x < kChainHalf * 32)
-            symbolic_hash_kernel_body<IT, 11, kChainHalf>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                          kClassHash0 + 3, c.rowptrC, err, bid,
-                                                          nb);
-        __syncthreads();
+        using K = typename KeyT<IT>::type;
+        chain_sym_bin<IT, K, 6>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 8>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 10>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 11>(c, err, bid, nb);
         if (c.LB > 0) {
             segtab_kernel_body<IT>(c.LB, c.D, c.bb, c.nprod, c.W, c.segtab, c.cnt, bid, nb);
             runlen_kernel_body<IT>(c.LB, c.D, c.bb, c.nprod, c.W, c.runlen, c.nextrun, c.cnt, bid,
@@ -242,29 +268,10 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         // numeric phase
         IT* colC = (IT*)c.colC;
         V* valC = (V*)c.valC;
-        numeric_hash_kernel_body<IT, V, 6, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                        kClassHash0, c.rowptrC, c.capacity, colC,
-                                                        valC, err, nullptr, nullptr, nullptr,
-                                                        bid, nb);
-        __syncthreads();
-        numeric_hash_kernel_body<IT, V, 8, kChainWarps>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                        kClassHash0 + 1, c.rowptrC, c.capacity,
-                                                        colC, valC, err, nullptr, nullptr,
-                                                        nullptr, bid, nb);
-        __syncthreads();
-        if (threadIdx.x < kChainHalf * 32)
-            numeric_hash_kernel_body<IT, V, 10, kChainHalf>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                            kClassHash0 + 2, c.rowptrC,
-                                                            c.capacity, colC, valC, err, nullptr,
-                                                            nullptr, nullptr, bid, nb);
-        __syncthreads();
-        // the largest hash bin keeps the 4-warp table layout of its standalone
-        // kernel (its tables fill the shared memory)
-        if (threadIdx.x < 128)
-            numeric_hash_kernel_body<IT, V, 11, 4>(c.D, c.rb, c.nprod, c.rows, c.cnt,
-                                                   kClassHash0 + 3, c.rowptrC, c.capacity, colC,
-                                                   valC, err, nullptr, nullptr, nullptr, bid, nb);
-        __syncthreads();
+        chain_num_bin<IT, V, K, 6>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 8>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 10>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 11>(c, colC, valC, err, bid, nb);
         if (c.W == kDenseW0)
             numeric_dense_kernel_body<IT, V, kDenseW0, kChainWarps>(
                 c.D, c.rb, c.nprod, c.rows, c.cnt, c.chunkcnt, c.segtab, c.runlen, c.nextrun,
@@ -284,11 +291,16 @@ template <class IT, class V>
 size_t chain_smem_bytes(int max_words) {
     using K = typename KeyT<IT>::type;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t b = (size_t)kChainWarps * (1u << 10) * sizeof(K);                      // symbolic bin 2
-    b = std::max(b, (size_t)kChainHalf * (1u << 11) * sizeof(K));                   // symbolic bin 3
-    b = std::max(b, (size_t)kChainWarps * ((1u << 8) * (sizeof(K) + vb) + 1024));   // numeric bin 1
-    b = std::max(b, (size_t)kChainHalf * ((1u << 10) * (sizeof(K) + vb) + 1024));   // numeric bin 2
-    b = std::max(b, (size_t)4 * ((1u << 11) * (sizeof(K) + vb) + 1024));            // numeric bin 3
+    auto bin = [&](int log2t, int warps, bool numeric) {
+        return (size_t)warps * (((size_t)1 << log2t) * (sizeof(K) + (numeric ? vb : 0)) +
+                                (numeric ? 1024 : 0));
+    };
+    size_t b = 0;
+    b = std::max(b, bin(10, chain_bin_warps<K, NoVal, 10, false>(), false));
+    b = std::max(b, bin(11, chain_bin_warps<K, NoVal, 11, false>(), false));
+    b = std::max(b, bin(8, chain_bin_warps<K, V, 8, true>(), true));
+    b = std::max(b, bin(10, chain_bin_warps<K, V, 10, true>(), true));
+    b = std::max(b, bin(11, chain_bin_warps<K, V, 11, true>(), true));
     b = std::max(b, (size_t)kChainWarps * ((vb * kDenseW0) + kDenseW0 / 8 + 32 * sizeof(DenseRun<V>)));
     b = std::max(b, (size_t)kChainHalf * ((vb * kDenseW1) + kDenseW1 / 8 + 32 * sizeof(DenseRun<V>)));
     b = std::max(b, (size_t)max_words * 4);                                         // dense symbolic
