@@ -156,10 +156,10 @@ __device__ __forceinline__ void chain_scan_apply(int64_t* x, long long N, const 
             carry = t;
         }
         __syncthreads();
-        for (long long b0 = tile * kScanTile; b0 < min(N, (tile + 1) * kScanTile);
-             b0 += blockDim.x) {
+        const long long lim = min(N, (tile + 1) * kScanTile);
+        for (long long b0 = tile * kScanTile; b0 < lim; b0 += blockDim.x) {
             const long long idx = b0 + threadIdx.x;
-            const long long v = idx < N ? x[idx] : 0;
+            const long long v = idx < lim ? x[idx] : 0;
             const long long inc = warp_incl_scan(v);
             if (lane_id() == 31) ws[threadIdx.x >> 5] = inc;
             __syncthreads();
@@ -170,7 +170,7 @@ __device__ __forceinline__ void chain_scan_apply(int64_t* x, long long N, const 
             }
             __syncthreads();
             const long long excl = carry + ws[threadIdx.x >> 5] + inc - v;
-            if (idx < N) x[idx] = excl;
+            if (idx < lim) x[idx] = excl;
             __syncthreads();
             if (threadIdx.x == blockDim.x - 1) carry = excl + v;
             __syncthreads();
@@ -187,14 +187,17 @@ __device__ __forceinline__ void chain_zero_rows(const ChainProduct& c, long long
 }
 
 // Warps of the persistent block that run a hash bin with tables of 2^LOG2T
-// slots: all 16 while their tables fit the shared-memory budget, else 8, else
-// 4 (the others wait at the stage's end).
+// slots: all of them while their tables fit the shared-memory budget, else
+// half, a quarter or an eighth (the others wait at the stage's end).
 constexpr size_t kChainSmemBudget = 208 * 1024;
 template <class K, class V, int LOG2T, bool NUMERIC>
 constexpr int chain_bin_warps() {
     constexpr size_t vb = NUMERIC && VOps<V>::has_val ? sizeof(V) : 0;
     constexpr size_t per = (size_t(1) << LOG2T) * (sizeof(K) + vb) + (NUMERIC ? 1024 : 0);
-    return 16 * per <= kChainSmemBudget ? 16 : 8 * per <= kChainSmemBudget ? 8 : 4;
+    return kChainWarps * per <= kChainSmemBudget       ? kChainWarps
+           : (kChainWarps / 2) * per <= kChainSmemBudget ? kChainWarps / 2
+           : (kChainWarps / 4) * per <= kChainSmemBudget ? kChainWarps / 4
+                                                          : kChainWarps / 8;
 }
 
 // One hash bin of the symbolic / numeric stage on the warps its tables allow.

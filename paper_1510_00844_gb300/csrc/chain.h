@@ -7,7 +7,7 @@
 
 namespace sg {
 
-constexpr int kChainThreads = 512;   // 16 warps per persistent block
+constexpr int kChainThreads = 768;   // 24 warps per persistent block
 constexpr int kChainWarps = kChainThreads / 32;
 // Warps of the persistent block that run a stage whose per-warp shared
 // memory would not fit 16 times (the largest hash bins, wide dense chunks);
