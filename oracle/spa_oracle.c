@@ -325,8 +325,9 @@ int oracle_sum_fill(int c, int64_t m, int64_t n, const int64_t* const* rps,
         for (int64_t i = 0; i < m; ++i) {
             int64_t nz = 0;
             for (int s = 0; s < c; ++s) {
-                const double* vd = (const double*)vs[s];
-                const uint64_t* vi = (const uint64_t*)vs[s];
+                /* pattern-only sums pass no value arrays (vs may be NULL) */
+                const double* vd = vs ? (const double*)vs[s] : NULL;
+                const uint64_t* vi = vs ? (const uint64_t*)vs[s] : NULL;
                 for (int64_t q = rps[s][i]; q < rps[s][i + 1]; ++q) {
                     int64_t j = cis[s][q];
                     int first = stamp[j] != i;

@@ -295,6 +295,21 @@ def test_mcl_prune_renorm():
             assert abs(Q.val[a:b].sum() - 1.0) <= 1e-13
 
 
+def test_pattern_only_sum_of_partials_is_the_union():
+    """The Boolean sum of partial products is the union of their patterns
+    (Sec. 4.3's merge with duplicate reduction, (or, and) semiring), checked
+    against a set union row by row."""
+    A = inputs.rmat(8).pattern()
+    parts = [oracle.spgemm(As, Bs, semiring="or_and") for As, Bs in oracle.kslice(A, A, 3)]
+    S = oracle.sum_partials(parts, semiring="or_and")
+    assert S.val is None
+    for i in range(A.nrows):
+        u = set()
+        for P in parts:
+            u |= set(np.asarray(P.col)[P.rowptr[i]:P.rowptr[i + 1]].tolist())
+        assert np.asarray(S.col)[S.rowptr[i]:S.rowptr[i + 1]].tolist() == sorted(u)
+
+
 def test_mcl_prune_keeps_entries_equal_to_threshold():
     """Pruning drops entries strictly below the threshold: an entry exactly at
     1e-4 stays.  Hand-written 2 x 4 case: row 0 holds 1e-4 (kept), 9.9e-5
