@@ -116,7 +116,11 @@ typedef struct {
                                 segments, one warp each; 0 = chosen per plan from
                                 the flops and the resident warps (16 for device-sized
                                 plans), else 10..22 */
-    int32_t reserved[1];     /* must be zero */
+    int32_t merge_staged;    /* merge numeric pass (c <= 4 lists in 16-byte aligned arrays):
+                                nonzero stages every list's entries in shared memory with
+                                bulk asynchronous copies (cp.async.bulk, mbarrier waits bounded,
+                                SPGEMM_ERR_TIMEOUT from spgemm_merge_check if one expires);
+                                0 keeps register windows (measured faster on GB300) */
 } spgemm_opts;
 
 typedef struct spgemm_plan_s* spgemm_plan_t;

@@ -667,8 +667,10 @@ spgemm_status spgemm_merge_numeric(int32_t c, const spgemm_csr* parts, const spg
     int sms = device_sm_count(nullptr);
     SG_CUDA(cudaMemsetAsync(&cnt->work_counter[1], 0, sizeof(unsigned long long),
                             (cudaStream_t)stream), "merge: memset");
+    const bool staged = opts && opts->merge_staged;
     cudaError_t e = sg::launch_merge(c, parts, vt, m, n, sms, (cudaStream_t)stream, true, nullptr,
-                                     rowptrC, colC, valC, &cnt->err, &cnt->work_counter[1]);
+                                     rowptrC, colC, valC, &cnt->err, &cnt->work_counter[1],
+                                     staged);
     if (e != cudaSuccess) return cuda_fail(e, "merge numeric");
     return SPGEMM_OK;
 }
@@ -679,6 +681,8 @@ spgemm_status spgemm_merge_check(void* stream, void* ws) {
     SG_CUDA(cudaMemcpyAsync(&herr, &((sg::DevCounters*)ws)->err, sizeof(int), cudaMemcpyDeviceToHost,
                             (cudaStream_t)stream), "merge check");
     SG_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "merge check");
+    if (herr == sg::kDevWaitTimeout)
+        return fail(SPGEMM_ERR_TIMEOUT, "a staged merge waited longer than its bound for a copy");
     if (herr) return fail(SPGEMM_ERR_INTERNAL, "device check failed in merge (code %d)", herr);
     return SPGEMM_OK;
 }

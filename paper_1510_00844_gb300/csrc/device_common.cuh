@@ -23,6 +23,7 @@ enum DevErr : int {
     kDevCapacity = 5,    // C did not fit the output capacity
     kDevArena = 6,       // a dense row is longer than the cursor arena slot
     kDevTooWide = 7,     // a dense row in a product wider than the shared-memory bitmap
+    kDevWaitTimeout = 9, // a bounded wait for asynchronous copies gave up
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

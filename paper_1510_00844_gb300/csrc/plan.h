@@ -140,7 +140,8 @@ cudaError_t launch_numeric(Plan& P, unsigned char* ws, const int64_t* rpC, long 
 cudaError_t launch_merge(int c, const spgemm_csr* parts, int vt, long long m, long long n,
                          int sm_count, cudaStream_t s, bool numeric, int64_t* rowcnt,
                          const int64_t* rpC, void* colC, void* valC, int* err,
-                         unsigned long long* work);  // work: zeroed row counter
+                         unsigned long long* work,   // work: zeroed row counter
+                         bool staged = false);       // numeric: stage lists by bulk copies
 template <class IT>
 cudaError_t launch_kslice_bounds(const spgemm_csr& A, int c, int64_t* bounds, int sm_count,
                                  cudaStream_t s);

@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("semiring", ctypes.c_int32), ("checked", ctypes.c_int32),
                 ("dense_chunk", ctypes.c_int32), ("dense_min_flops", ctypes.c_int32),
                 ("max_row_nnz", ctypes.c_int32), ("hash_shift", ctypes.c_int32),
-                ("seg_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("seg_log2", ctypes.c_int32), ("merge_staged", ctypes.c_int32)]
 
 
 @dataclass(frozen=True)
@@ -864,9 +864,12 @@ def merge_symbolic_static(parts: Sequence[DeviceCSR], semiring: int = PLUS_TIMES
 
 def merge_numeric(parts: Sequence[DeviceCSR], ws: torch.Tensor, rowptrC: torch.Tensor,
                   colC: torch.Tensor, valC: Optional[torch.Tensor], semiring: int = PLUS_TIMES,
-                  stream=None) -> None:
+                  stream=None, staged: bool = False) -> None:
+    """spgemm_merge_numeric; staged: entries staged in shared memory by bulk
+    asynchronous copies (spgemm_opts.merge_staged)."""
     arr = _parts(parts)
     opts = _Opts(semiring, 0)
+    opts.merge_staged = 1 if staged else 0
     _check(_lib.spgemm_merge_numeric(len(parts), arr, ctypes.byref(opts), _stream(stream),
                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                      ctypes.c_void_p(rowptrC.data_ptr()),
