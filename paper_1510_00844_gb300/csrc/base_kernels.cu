@@ -27,7 +27,9 @@ __global__ void class_offsets_kernel(DevCounters* cnt, int seg_log2) {
 // Scatter global row ids into their class segment (order inside a class is
 // free; rows are independent).  Each block counts its rows per class in
 // shared memory, reserves one range per class with a single global atomic,
-// then places its rows.
+// then places its rows.  Lanes of a warp with the same class are grouped, so
+// one atomic per class and warp does the counting (rows of one product often
+// share a class).
 __global__ void bin_rows_kernel(long long R, const unsigned char* __restrict__ cls,
                                 int32_t* __restrict__ rows, DevCounters* cnt) {
     __shared__ unsigned long long loc[kNumClasses];
@@ -37,17 +39,14 @@ __global__ void bin_rows_kernel(long long R, const unsigned char* __restrict__ c
     const long long r1 = min(R, r0 + per_block);
     for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) loc[t] = 0;
     __syncthreads();
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(&loc[cls[r]], 1ull);
+    bin_block_rows(cls, rows, r0, r1, loc, nullptr);
     __syncthreads();
     for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) {
         base[t] = loc[t] ? atomicAdd(&cnt->class_cursor[t], loc[t]) : 0;
         loc[t] = 0;
     }
     __syncthreads();
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int c = cls[r];
-        rows[base[c] + atomicAdd(&loc[c], 1ull)] = (int32_t)r;
-    }
+    bin_block_rows(cls, rows, r0, r1, loc, base);
 }
 
 // ------------------------------------------------------------------ scan

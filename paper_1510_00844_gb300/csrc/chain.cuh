@@ -102,17 +102,14 @@ __device__ __forceinline__ void chain_bin(const ChainProduct& c, long long bid, 
     const long long per_block = (c.R + nb - 1) / nb;
     const long long r0 = bid * per_block;
     const long long r1 = min(c.R, r0 + per_block);
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(&loc[c.cls[r]], 1ull);
+    bin_block_rows(c.cls, c.rows, r0, r1, loc, nullptr);
     __syncthreads();
     for (int t = threadIdx.x; t < kNumClasses; t += blockDim.x) {
         base[t] = off[t] + (loc[t] ? atomicAdd(&cnt->class_cursor[t], loc[t]) : 0ull);
         loc[t] = 0;
     }
     __syncthreads();
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int cl = c.cls[r];
-        c.rows[base[cl] + atomicAdd(&loc[cl], 1ull)] = (int32_t)r;
-    }
+    bin_block_rows(c.cls, c.rows, r0, r1, loc, base);
 }
 
 // Row-pointer scan, first stage: sums of tiles of kScanTile entries.

@@ -123,6 +123,28 @@ __device__ __forceinline__ RowCtx<IT, V> row_ctx(const ProdDesc* __restrict__ D,
     return c;
 }
 
+// Rows [r0, r1) of a block by class: with base == nullptr, count them per
+// class into loc; else place row r at base[c] + a slot taken from loc[c].
+// Lanes of a warp with the same class take one atomic together.
+__device__ __forceinline__ void bin_block_rows(const unsigned char* __restrict__ cls,
+                                               int32_t* __restrict__ rows, long long r0,
+                                               long long r1, unsigned long long* loc,
+                                               const unsigned long long* base) {
+    const int lane = threadIdx.x & 31;
+    for (long long b = r0 + (threadIdx.x & ~31); b < r1; b += blockDim.x) {
+        const long long r = b + lane;
+        const bool valid = r < r1;
+        const int c = valid ? (int)cls[r] : -1 - lane;
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(grp) - 1;
+        const int rank = __popc(grp & ((1u << lane) - 1u));
+        unsigned long long first = 0;
+        if (valid && lane == leader) first = atomicAdd(&loc[c], (unsigned long long)__popc(grp));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (valid && base) rows[base[c] + first + rank] = (int32_t)r;
+    }
+}
+
 // Tile of the int64 exclusive scan: 256 threads x 16 items.
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
