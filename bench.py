@@ -820,12 +820,26 @@ def run_profile_leg(args):
             nnz = sum(C.nnz for C in sg.batch_spgemm(As, Bs))
             torch.cuda.synchronize()
         print(f"batched {len(pairs)} ER products: nnz {nnz}", flush=True)
-    elif leg in ("amg", "mis2"):
+    elif leg == "batched-chain":
+        pairs = inputs.batched_er(512)[: max(1, min(512, args.products))]
+        As = [sg.to_device(a) for a, _ in pairs]
+        Bs = [sg.to_device(b) for _, b in pairs]
+        cap = int(sg.batch_plan(As, Bs).info()["flops"])
+        dp = sg.device_plan(As, Bs, max_row_nnz=4096)
+        rp = torch.empty(dp.R + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(cap, dtype=As[0].col.dtype, device="cuda")
+        val = torch.empty(cap, dtype=As[0].val.dtype, device="cuda")
+        ch = sg.Chain([(dp, rp, cap, col, val)])
+        for _ in range(reps):
+            ch.launch()
+            ch.check()
+        print(f"batched chain {len(pairs)} ER products: nnz {int(rp[-1].item())}", flush=True)
+    elif leg in ("amg", "amg-chain", "mis2"):
         N = 128
         dA0 = sg.to_device(inputs.laplacian_7pt(N))
-        if leg == "amg":
+        if leg in ("amg", "amg-chain"):
             dRs = [sg.to_device(inputs.aggregation_2x2x2(N >> l)) for l in range(3)]
-            chain = amg.GalerkinChain(dA0, dRs, torch.cuda.Stream())
+            chain = amg.GalerkinChain(dA0, dRs, torch.cuda.Stream(), persistent=leg == "amg-chain")
             chain.capture()
             for _ in range(reps):
                 chain.replay()
@@ -857,7 +871,8 @@ def main():
                     help="compare every k-th MCL panel against the exact two-phase path")
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the split / batched / AMG comparisons")
-    ap.add_argument("--profile-leg", choices=["product", "kslice", "batched", "amg", "mis2"],
+    ap.add_argument("--profile-leg", choices=["product", "kslice", "batched", "batched-chain",
+                                              "amg", "amg-chain", "mis2"],
                     help="run one workload --reps times without timing (for ncu captures)")
     ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of --profile-leg")
     ap.add_argument("--reps", type=int, default=2, help="runs of --profile-leg")
