@@ -293,6 +293,57 @@ def _timed(torch, fn, reps):
     return best
 
 
+def merge_roofline(sg, torch, dA, c=4, reps=3):
+    """The multiway merge alone on the 4 k-slice partials of the product
+    (count + scan + numeric, then the numeric pass by itself), register
+    windows against lists staged in shared memory by bulk asynchronous
+    copies.  Algorithmic bytes of the numeric pass: every partial entry read
+    once and every entry of C written once (index + value each), plus the c
+    partial row-pointer arrays and rowptr(C)."""
+    _, parts = sg.spgemm_kslice(dA, dA, c)
+    torch.cuda.synchronize()
+    m = dA.nrows
+    ws = sg.merge_workspace(len(parts), m, dA.ncols, dA.rowptr.device)
+    rowptrC, nnz = sg.merge_symbolic(parts, ws)
+    colC = torch.empty(nnz, dtype=parts[0].col.dtype, device="cuda")
+    valC = torch.empty(nnz, dtype=parts[0].val.dtype, device="cuda")
+    ent = parts[0].col.element_size() + parts[0].val.element_size()
+    nparts = sum(int(p.nnz) for p in parts)
+    nbytes = ent * (nparts + int(nnz)) + 8 * (m + 1) * (len(parts) + 1)
+    stream = torch.cuda.current_stream()
+    hbm, _ = peaks()
+    res = {"partial_entries": nparts, "nnz_C": int(nnz), "algorithmic_bytes": int(nbytes)}
+    for name, staged in (("windows", False), ("staged", True)):
+        sg.merge_numeric(parts, ws, rowptrC, colC, valC, staged=staged)
+        sg.merge_check(ws)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sg.merge_numeric(parts, ws, rowptrC, colC, valC, staged=staged)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        avg = float(np.mean(ms))
+        res[name] = {"numeric_ms": round(avg, 3),
+                     "gbs": round(nbytes / (avg * 1e-3) / 1e9, 1),
+                     "frac_of_measured_hbm": round(nbytes / (avg * 1e-3) / 1e9 / hbm, 4)}
+    del parts, colC, valC, ws
+    return res
+
+
+def _stage_report(stages):
+    """Stage times of a persistent chain's last launch (block 0's
+    %globaltimer at every barrier): totals per stage kind over the products,
+    and per product."""
+    by_stage, by_step = {}, {}
+    for q, name, ms in stages:
+        by_stage[name] = round(by_stage.get(name, 0.0) + ms, 4)
+        if q >= 0:
+            by_step[str(q)] = round(by_step.get(str(q), 0.0) + ms, 4)
+    return {"by_stage": by_stage, "by_product": by_step}
+
+
 def run_paths(args, A, dA, sg, torch):
     """The other rows of the path, each against its plain counterpart:
     k=4 split + merge on the same product, 512 uneven ER products batched vs
@@ -309,6 +360,7 @@ def run_paths(args, A, dA, sg, torch):
     out["kslice4_merge_rmat18"] = {"ms": round(t * 1e3, 3),
                                    "gflops": round(2 * flops / t / 1e9, 3),
                                    "hypersparse_slices_ms": round(th * 1e3, 3),
+                                   "merge": merge_roofline(sg, torch, dA),
                                    "note": "4 k-slice partial products + multiway merge; "
                                            "hypersparse: slices as DCSR views"}
     pairs = inputs.batched_er(512)
@@ -340,12 +392,13 @@ def run_paths(args, A, dA, sg, torch):
             and bool((valC[:nnz] == torch.cat([C.val for C in ref])).all()))
     # the same device-sized plan as one persistent chain launch
     colC.fill_(-1)
-    chain = sg.Chain([(dp, rowptrC, int(bflops), colC, valC)])
+    chain = sg.Chain([(dp, rowptrC, int(bflops), colC, valC)], record_stages=True)
     with torch.cuda.stream(gs):
         chain.launch(gs)
     chain.check(gs)
     tpc = _timed(torch, lambda: chain.launch(gs), reps)
     chain.check(gs)
+    batch_stages = _stage_report(chain.stage_ms())
     same_chain = (int(rowptrC[-1].item()) == nnz
                   and bool((colC[:nnz] == torch.cat([C.col for C in ref])).all())
                   and bool((valC[:nnz] == torch.cat([C.val for C in ref])).all()))
@@ -361,6 +414,7 @@ def run_paths(args, A, dA, sg, torch):
                                 "persistent_launches": 1,
                                 "persistent_bit_identical": bool(same_chain),
                                 "persistent_speedup_vs_sequential": round(ts / tpc, 3),
+                                "persistent_stage_ms": batch_stages,
                                 "f32_error": f32_error,
                                 "autotune": _tuning_report(best, table)}
     del As, Bs, pairs
@@ -376,13 +430,14 @@ def run_paths(args, A, dA, sg, torch):
     chain.check()
     # the six products of the hierarchy in one persistent launch (the
     # transposes R_l^T depend only on the given R_l and are formed once)
-    pchain = amg.GalerkinChain(dA0, dRs, s, persistent=True)
+    pchain = amg.GalerkinChain(dA0, dRs, s, persistent=True, record_stages=True)
     pchain.capture()
     pchain.replay()
     torch.cuda.synchronize()
     pchain.check()
     tpg = _timed(torch, pchain.replay, 5)
     pchain.check()
+    amg_stages = _stage_report(pchain.chain.stage_ms())
     same_p = all(bool(torch.equal(C.col, D.col)) and bool(torch.equal(C.val, D.val))
                  for C, D in zip(pchain.results(), chain.results()))
     tr_graph = torch.cuda.CUDAGraph()
@@ -415,6 +470,7 @@ def run_paths(args, A, dA, sg, torch):
                                             "persistent_ms": round(tpg * 1e3, 3),
                                             "persistent_launches": 1,
                                             "persistent_bit_identical": bool(same_p),
+                                            "persistent_stage_ms": amg_stages,
                                             "transposes_ms": round(ttr * 1e3, 3),
                                             "note": "graph_ms: transposes and both products of "
                                                     "every level as one captured graph of "

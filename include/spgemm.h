@@ -235,6 +235,14 @@ typedef struct {
     double timeout_s;       /* bound of every barrier wait; 0 = 10 s */
     int32_t withhold_stage; /* -1, or a stage whose completion is withheld (tests) */
     int32_t reserved;
+    /* NULL, or a device array of 2 + 6 * nsteps uint64 that every launch
+     * fills with %globaltimer readings (ns) of block 0: [0] at its start,
+     * [1 + s] when it passed the barrier after stage s (stage 0 clears the
+     * counters; product p's stages are 1 + 6p .. 6 + 6p: analysis, binning,
+     * symbolic, scan sums, scan apply, numeric).  Caller-owned, kept until
+     * the chain is destroyed; entries of stages not reached are left as
+     * they were. */
+    uint64_t* stage_ns;
 } spgemm_chain_opts;
 
 typedef struct spgemm_chain_s* spgemm_chain_t;

@@ -27,7 +27,8 @@ class GalerkinChain:
 
     def __init__(self, A0: sg.DeviceCSR, Rs: List[sg.DeviceCSR], stream: torch.cuda.Stream,
                  max_row_nnz: int = 64, tuning: Optional[sg.Tuning] = None,
-                 persistent: bool = False, timeout_s: float = 0.0):
+                 persistent: bool = False, timeout_s: float = 0.0,
+                 record_stages: bool = False):
         self.stream = stream
         self.persistent = persistent
         self.Rs = Rs
@@ -67,7 +68,7 @@ class GalerkinChain:
             for lv in self.levels:
                 steps.append((lv["p1"], lv["T"].rowptr, lv["cap"], lv["T"].col, lv["T"].val))
                 steps.append((lv["p2"], lv["A"].rowptr, lv["cap"], lv["A"].col, lv["A"].val))
-            self.chain = sg.Chain(steps, timeout_s=timeout_s)
+            self.chain = sg.Chain(steps, timeout_s=timeout_s, record_stages=record_stages)
 
     def _transpose(self, lv):
         Rt = lv["Rt"]

@@ -152,6 +152,7 @@ spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps
     hs.timeout_ns = (unsigned long long)(t * 1e9);
     hs.withhold = o.withhold_stage;
     hs.nsteps = nsteps;
+    hs.stamps = reinterpret_cast<unsigned long long*>(o.stage_ns);
     cudaError_t e = cudaMemcpy(C->sync, &hs, sizeof(hs), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(C->steps, host.data(), host.size() * sizeof(sg::ChainProduct),

@@ -63,6 +63,7 @@ __device__ __forceinline__ bool chain_barrier(ChainSync* s, int idx) {
             __nanosleep(128);
         }
         ok = res;
+        if (res && blockIdx.x == 0 && s->stamps) s->stamps[idx + 1] = globaltimer_ns();
     }
     __syncthreads();
     __threadfence();   // every thread orders its later loads after the barrier
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kChainThreads, 1)
     chain_kernel(const ChainProduct* __restrict__ steps, ChainSync* sync) {
     const long long bid = blockIdx.x, nb = gridDim.x;
     const int nsteps = sync->nsteps;
+    if (bid == 0 && threadIdx.x == 0 && sync->stamps) sync->stamps[0] = globaltimer_ns();
     int stage = 0;
     // stage 0: counters of every product and the last row pointer to zero
     for (int p = 0; p < nsteps; ++p) {

@@ -51,6 +51,7 @@ struct ChainSync {
     unsigned long long timeout_ns;
     int withhold;           // stage whose completion no block signals (-1: none)
     int nsteps;
+    unsigned long long* stamps;  // NULL, or 2 + 6 * nsteps %globaltimer readings
 };
 
 template <class IT, class V>

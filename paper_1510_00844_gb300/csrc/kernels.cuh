@@ -32,6 +32,9 @@ constexpr int kClassHash0 = 1;
 constexpr int kClassDense0 = kClassHash0 + kNumHashBins;          // largest-flops bucket
 constexpr int kNumClasses = kClassDense0 + (kDenseMaxLog2 - kDenseMinLog2 + 1);
 constexpr int kSegGrid = 16;
+// Table size (log2 slots) of hash bin 0, whose rows (at most 32 products)
+// take the table-free short-row path instead.
+constexpr int kShortLog2T = 6;
 // Dense chunk configurations (columns per chunk, warps per block): one is
 // chosen per plan (spgemm_opts.dense_chunk forces one).
 constexpr int kDenseW0 = 1024, kDenseWarps0 = 8;
@@ -271,8 +274,12 @@ __device__ __forceinline__ void analyze_kernel_body(long long R, const ProdDesc*
             flops_out[r] = f;
             if (cap_out) cap_out[r] = prm ? cap : f;
             int cl = row_class(f, dense_min, hash_shift);
-            if (prm && cl > kClassEmpty && cl < kClassDense0)
+            if (prm && cl > kClassEmpty && cl < kClassDense0) {
                 cl = row_class(cap > 0 ? cap : 1, dense_min, hash_shift);
+                // bin 0 is the short-row path (one product per lane): a row
+                // with more products takes bin 1's table whatever its size
+                if (cl == kClassHash0 && f > 32) cl = kClassHash0 + 1;
+            }
             cls_out[r] = (unsigned char)cl;
             if (cl >= kClassDense0) {
                 if (c.n > max_dense_n) blk_unsup = 1;
@@ -365,6 +372,148 @@ __global__ void validate_kernel(long long m, long long ncols, long long nnz, con
     }
 }
 
+// ------------------------------------------ short rows (hash bin 0)
+// A row of at most 32 products needs no table.  Lane x takes the row's x-th
+// product in ascending k (then in B(k,:)'s order): the A entries are read in
+// batches of 32 and each batch's products are flattened onto the lanes after
+// those of earlier batches; the owner of product f is the last entry whose
+// exclusive prefix of run lengths is <= f (a five-step search over the
+// lanes, always a lane of the batch).  Equal columns are then grouped with
+// __match_any_sync.  Returns the number of products, or -1 if the row has
+// more than 32 (a row of hash bin 0 never does).
+template <class IT, class V, bool VALS>
+__device__ __forceinline__ int short_row_gather(const RowCtx<IT, V>& c,
+                                                typename KeyT<IT>::type& key, V& v) {
+    using K = typename KeyT<IT>::type;
+    const int lane = lane_id();
+    int have = 0;
+    key = K(-1);
+    v = VOps<V>::init();
+    for (long long b = c.a0; b < c.a1; b += 32) {
+        const int nb = (int)min(32LL, c.a1 - b);
+        long long lo = 0;
+        int len = 0;
+        V a = VOps<V>::init();
+        if (lane < nb) {
+            const long long k = (long long)c.ciA[b + lane];
+            lo = c.rpB[k];
+            len = (int)min(c.rpB[k + 1] - lo, 33LL);
+            if constexpr (VALS) a = load_val(c.vA, b + lane);
+        }
+        const int incl = warp_incl_scan(len);
+        const int tot = __shfl_sync(kFull, incl, 31);
+        if (tot == 0) continue;
+        if (have + tot > 32) return -1;
+        const int excl = incl - len;
+        const int f = lane - have;
+        int e = 0;
+#pragma unroll
+        for (int w = 16; w; w >>= 1) {
+            const int cand = e + w;
+            const int ex = __shfl_sync(kFull, excl, cand & 31);
+            if (cand < nb && ex <= f) e = cand;
+        }
+        const long long lo_e = __shfl_sync(kFull, lo, e);
+        const int ex_e = __shfl_sync(kFull, excl, e);
+        const V a_e = shfl_val(a, e);
+        if (f >= 0 && f < tot) {
+            const long long q = lo_e + (f - ex_e);
+            key = (K)c.ciB[q];
+            if constexpr (VALS) v = VOps<V>::mul(a_e, load_val(c.vB, q));
+        }
+        have += tot;
+    }
+    return have;
+}
+
+// Symbolic count of a short row: the number of distinct columns.
+template <class IT>
+__device__ __forceinline__ void short_row_symbolic(const RowCtx<IT, NoVal>& c, long long r,
+                                                   int64_t* __restrict__ rowcnt, int* err) {
+    using K = typename KeyT<IT>::type;
+    const int lane = lane_id();
+    K key;
+    NoVal v;
+    const int np = short_row_gather<IT, NoVal, false>(c, key, v);
+    if (np < 0) {
+        if (lane == 0) atomicExch(err, (int)kDevTableFull);
+        return;
+    }
+    const bool valid = lane < np;
+    const K kk = valid ? key : (K)(-1 - lane);
+    const unsigned grp = __match_any_sync(kFull, kk);
+    const bool leader = valid && (grp & lanemask_lt()) == 0u;
+    const int cnt = __popc(__ballot_sync(kFull, leader));
+    if (lane == 0) rowcnt[r] = cnt;
+}
+
+// Numeric pass of a short row: the lowest lane of each group of equal
+// columns adds the group's products in lane order from the identity (the
+// order in which the hash path adds them), and writes its column at the
+// number of groups with a smaller column.  Slot mode as in the hash path.
+template <class IT, class V>
+__device__ __forceinline__ void short_row_numeric(const RowCtx<IT, V>& c, long long r,
+                                                  const int64_t* __restrict__ rpC, long long cap,
+                                                  IT* __restrict__ ciC, V* __restrict__ vC,
+                                                  int* err, int64_t* __restrict__ rowend,
+                                                  int32_t* __restrict__ overflow,
+                                                  unsigned* overflow_count) {
+    using K = typename KeyT<IT>::type;
+    constexpr bool HV = VOps<V>::has_val;
+    const int lane = lane_id();
+    K key;
+    V v;
+    const int np = short_row_gather<IT, V, HV>(c, key, v);
+    if (np < 0) {
+        if (lane == 0) atomicExch(err, (int)kDevTableFull);
+        return;
+    }
+    const bool valid = lane < np;
+    const K kk = valid ? key : (K)(-1 - lane);
+    const unsigned grp = __match_any_sync(kFull, kk);
+    const bool leader = valid && (grp & lanemask_lt()) == 0u;
+    const unsigned L = __ballot_sync(kFull, leader);
+    const int cnt = __popc(L);
+    V sum = VOps<V>::init();
+    if constexpr (HV) {
+        unsigned rem = leader ? grp : 0u;
+        const int maxc = (int)__reduce_max_sync(kFull, (unsigned)__popc(rem));
+        for (int t = 0; t < maxc; ++t) {
+            const int src = rem ? __ffs(rem) - 1 : lane;
+            const V x = shfl_val(v, src);
+            if (rem) {
+                sum = VOps<V>::add(sum, x);
+                rem &= rem - 1u;
+            }
+        }
+    }
+    int pos = 0;
+    for (unsigned Lr = L; Lr; Lr &= Lr - 1u) {
+        const K kj = __shfl_sync(kFull, kk, __ffs(Lr) - 1);
+        pos += kj < kk ? 1 : 0;
+    }
+    const long long out = rpC[r];
+    long long rcnt = rpC[r + 1] - out;
+    if (rowend != nullptr) {
+        if (cnt > rcnt) {
+            if (lane == 0) {
+                overflow[atomicAdd(overflow_count, 1u)] = (int32_t)r;
+                rowend[r] = -1;
+            }
+            return;
+        }
+        rcnt = cnt;
+        if (lane == 0) rowend[r] = out + cnt;
+    } else if (cnt != rcnt && lane == 0) {
+        atomicExch(err, (int)kDevCountMismatch);
+    }
+    if (out + rcnt > cap && lane == 0) atomicExch(err, (int)kDevCapacity);
+    if (leader && pos < rcnt && out + pos < cap) {
+        ciC[out + pos] = (IT)kk;
+        if constexpr (HV) vC[out + pos] = sum;
+    }
+}
+
 // --------------------------------------------------- symbolic: hash rows
 // One warp per row; table of 2^LOG2T keys per warp.  Row count -> rowcnt[i].
 template <class IT, int LOG2T, int WARPS>
@@ -378,13 +527,21 @@ __device__ __forceinline__ void symbolic_hash_kernel_body(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
-    K* keys = reinterpret_cast<K*>(smem_raw) + (size_t)w * T;
-    for (int s = lane; s < T; s += 32) keys[s] = K(-1);
-    __syncwarp();
     const long long nrows = (long long)cnt->class_count[cls];
     const int32_t* crow = rows + cnt->class_off[cls];
     const long long gw = (long long)vbid * WARPS + w;
     const long long nw = (long long)vnb * WARPS;
+    if constexpr (LOG2T == kShortLog2T) {
+        // rows of at most 32 products: no table
+        for (long long rr = gw; rr < nrows; rr += nw) {
+            const long long r = crow[rr];
+            short_row_symbolic<IT>(row_ctx<IT, NoVal>(D, rb, nprod, r), r, rowcnt, err);
+        }
+        return;
+    }
+    K* keys = reinterpret_cast<K*>(smem_raw) + (size_t)w * T;
+    for (int s = lane; s < T; s += 32) keys[s] = K(-1);
+    __syncwarp();
     for (long long rr = gw; rr < nrows; rr += nw) {
         const long long r = crow[rr];
         const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
@@ -634,6 +791,19 @@ __device__ __forceinline__ void numeric_hash_kernel_body(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
+    if constexpr (LOG2T == kShortLog2T) {
+        // rows of at most 32 products: no table
+        const long long nrows = (long long)cnt->class_count[cls];
+        const int32_t* crow = rows + cnt->class_off[cls];
+        const long long gw = (long long)vbid * WARPS + w;
+        const long long nw = (long long)vnb * WARPS;
+        for (long long rr = gw; rr < nrows; rr += nw) {
+            const long long r = crow[rr];
+            short_row_numeric<IT, V>(row_ctx<IT, V>(D, rb, nprod, r), r, rpC, cap, ciC, vC, err,
+                                     rowend, overflow, overflow_count);
+        }
+        return;
+    }
     // layout per warp: T values (if any), T keys, 256 radix counters
     constexpr size_t vbytes = HV ? sizeof(V) * T : 0;
     unsigned char* base = smem_raw + (size_t)w * (vbytes + sizeof(K) * T + 256 * sizeof(int));

@@ -96,7 +96,7 @@ cudaError_t sym_hash_bin(Plan& P, int bin, int64_t* rowcnt) {
     if (P.device_sized && bin > 0 && (hash_bin_flops(bin - 1) >> P.hash_shift) >= P.dense_min)
         return cudaSuccess;
     auto k = symbolic_hash_kernel<IT, LOG2T, WARPS>;
-    size_t smem = (size_t)WARPS * (1u << LOG2T) * sizeof(K);
+    size_t smem = LOG2T == kShortLog2T ? 0 : (size_t)WARPS * (1u << LOG2T) * sizeof(K);
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);
@@ -188,7 +188,9 @@ cudaError_t num_hash_bin(Plan& P, int bin, const int64_t* rpC, long long cap, IT
         return cudaSuccess;
     auto k = numeric_hash_kernel<IT, V, LOG2T, WARPS>;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
-    size_t smem = (size_t)WARPS * ((1u << LOG2T) * (sizeof(K) + vb) + 256 * sizeof(int));
+    size_t smem = LOG2T == kShortLog2T
+                      ? 0
+                      : (size_t)WARPS * ((1u << LOG2T) * (sizeof(K) + vb) + 256 * sizeof(int));
     cudaError_t e = allow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int occ = occupancy_blocks(k, WARPS * 32, smem);

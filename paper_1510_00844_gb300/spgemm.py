@@ -338,7 +338,10 @@ class _ChainStep(ctypes.Structure):
 
 class _ChainOpts(ctypes.Structure):
     _fields_ = [("timeout_s", ctypes.c_double), ("withhold_stage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("stage_ns", ctypes.c_void_p)]
+
+
+CHAIN_STAGES = ("analysis", "binning", "symbolic", "scan sums", "scan apply", "numeric")
 
 
 class Chain:
@@ -346,9 +349,11 @@ class Chain:
     launch.  steps: (plan from device_plan, rowptrC, capacity, colC, valC); a
     step may read an earlier step's outputs.  launch() enqueues (capturable
     in a CUDA graph), check() waits and raises SpgemmError(TIMEOUT) when a
-    barrier wait expired."""
+    barrier wait expired.  With record_stages, every launch records when
+    block 0 passed each barrier; stage_ms() returns the stage durations."""
 
-    def __init__(self, steps, timeout_s: float = 0.0, withhold_stage: int = -1):
+    def __init__(self, steps, timeout_s: float = 0.0, withhold_stage: int = -1,
+                 record_stages: bool = False):
         self._steps = list(steps)
         dev = self._steps[0][1].device
         arr = (_ChainStep * len(self._steps))()
@@ -357,7 +362,10 @@ class Chain:
                                 col.data_ptr() if col is not None and col.numel() else None,
                                 None if val is None or val.numel() == 0 else val.data_ptr())
         self.ws = _workspace(_lib.spgemm_chain_workspace_size(len(self._steps)), dev)
-        opts = _ChainOpts(float(timeout_s), int(withhold_stage), 0)
+        self.stamps = (torch.zeros(2 + 6 * len(self._steps), dtype=torch.int64, device=dev)
+                       if record_stages else None)
+        opts = _ChainOpts(float(timeout_s), int(withhold_stage), 0,
+                          None if self.stamps is None else self.stamps.data_ptr())
         h = ctypes.c_void_p()
         _check(_lib.spgemm_chain_create(len(self._steps), arr, ctypes.byref(opts),
                                         ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
@@ -374,6 +382,19 @@ class Chain:
 
     def grid(self) -> int:
         return int(_lib.spgemm_chain_grid(self._h))
+
+    def stage_ms(self):
+        """[(step, stage name, ms)] of the last launch (record_stages), the
+        counter-clearing stage as step -1."""
+        if self.stamps is None:
+            raise ValueError("chain created without record_stages")
+        t = self.stamps.cpu().tolist()
+        out = [(-1, "clear", (t[1] - t[0]) * 1e-6)]
+        for q in range(len(self._steps)):
+            for j, name in enumerate(CHAIN_STAGES):
+                k = 1 + 6 * q + j
+                out.append((q, name, (t[k + 1] - t[k]) * 1e-6))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
@@ -883,14 +904,14 @@ def merge_check(ws: torch.Tensor, stream=None) -> None:
 
 
 def merge(parts: Sequence[DeviceCSR], semiring: int = PLUS_TIMES, stream=None,
-          verify: bool = False) -> DeviceCSR:
+          verify: bool = False, staged: bool = False) -> DeviceCSR:
     m, n = parts[0].nrows, parts[0].ncols
     ws = merge_workspace(len(parts), m, n, parts[0].rowptr.device)
     rowptrC, nnz = merge_symbolic(parts, ws, semiring, stream)
     pattern = semiring == OR_AND or parts[0].val is None
     colC = torch.empty(nnz, dtype=parts[0].col.dtype, device=ws.device)
     valC = None if pattern else torch.empty(nnz, dtype=parts[0].val.dtype, device=ws.device)
-    merge_numeric(parts, ws, rowptrC, colC, valC, semiring, stream)
+    merge_numeric(parts, ws, rowptrC, colC, valC, semiring, stream, staged=staged)
     if verify:
         merge_check(ws, stream)
     return DeviceCSR(m, n, rowptrC, colC, valC)

@@ -6,6 +6,7 @@ kernel launch with device-side barriers between phases.
   products, Boolean products, and the AMG Galerkin hierarchy (products that
   read the previous product's output), which also meets its closed form.
 * A chain captured in a CUDA graph replays correctly.
+* Stage stamps (record_stages) cover every barrier, in order.
 * The bounded wait: with one stage's completion withheld, every block gives
   up after the timeout, spgemm_chain_check reports TIMEOUT, and the context
   stays usable (the same chain then runs normally)."""
@@ -46,7 +47,7 @@ def test_chain_single_product_with_dense_rows(sg, scale, idt):
     assert sg.plan(dA, dA).info()["rows_dense"] > 0
     cap = int(oracle.row_flops(M, M).sum())
     rp, col, val = _outputs(sg, p, cap, dA.col.dtype, torch.float64)
-    ch = sg.Chain([(p, rp, cap, col, val)])
+    ch = sg.Chain([(p, rp, cap, col, val)], record_stages=True)
     R = oracle.spgemm(M, M)
     for _ in range(2):
         col.fill_(-1)
@@ -56,6 +57,11 @@ def test_chain_single_product_with_dense_rows(sg, scale, idt):
         assert_pattern_equal(C, R)
         assert np.array_equal(C.to_host()[2], R.val)
     assert ch.grid() >= 1
+    # stage stamps: every barrier passed, in order
+    st = ch.stage_ms()
+    assert [n for _, n, _ in st] == ["clear"] + list(sg.CHAIN_STAGES)
+    assert all(ms >= 0.0 for _, _, ms in st)
+    assert sum(ms for _, _, ms in st) > 0.0
 
 
 def test_chain_batch_matches_execute(sg):
