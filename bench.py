@@ -650,9 +650,12 @@ def run_e2e(args, A, sg, torch, dev, dP):
     from paper_1510_00844_gb300 import pipeline
     if dP is None:
         return None
-    hr = torch.from_numpy(A.rowptr).pin_memory()
-    hc = torch.from_numpy(A.col).pin_memory()
-    hv = torch.from_numpy(A.val).pin_memory()
+    hr = pipeline.pinned_empty(A.rowptr.size, torch.int64)
+    hc = pipeline.pinned_empty(A.col.size, torch.int32 if A.col.dtype == np.int32 else torch.int64)
+    hv = pipeline.pinned_empty(A.val.size, torch.float64)
+    hr.copy_(torch.from_numpy(A.rowptr))
+    hc.copy_(torch.from_numpy(A.col))
+    hv.copy_(torch.from_numpy(A.val))
     dr = torch.empty_like(hr, device=dev)
     dc = torch.empty_like(hc, device=dev)
     dv = torch.empty_like(hv, device=dev)
@@ -661,8 +664,9 @@ def run_e2e(args, A, sg, torch, dev, dP):
     h2d = hr.numel() * 8 + hc.numel() * hc.element_size() + hv.numel() * 8
     d2h = 0
     nsteps = max(1, min(args.steps, 2))
+    warm = 2     # the first copies into freshly registered pages run slow
     splits = []
-    for it in range(1 + nsteps):
+    for it in range(warm + nsteps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -681,7 +685,7 @@ def run_e2e(args, A, sg, torch, dev, dP):
         tm["wall_ms"] = (t1 - t0) * 1e3
         nnz = out_host.nnz
         d2h = (A.nrows + 1) * 8 + nnz * (out_host.col.element_size() + 8)
-        if it > 0:
+        if it >= warm:
             times.append(t1 - t0)
             splits.append(tm)
         del M
@@ -694,6 +698,9 @@ def run_e2e(args, A, sg, torch, dev, dP):
                        "first_numeric_to_last_copy_ms", "wall_ms")}
     split["h2d_gbs"] = round(h2d / (split["h2d_ms"] * 1e-3) / 1e9, 1)
     split["d2h_gbs"] = round(last["d2h_bytes"] / (split["copy_ms"] * 1e-3) / 1e9, 1)
+    split["per_step_wall_ms"] = [round(t["wall_ms"], 1) for t in splits]
+    split["per_step_plans_symbolic_ms"] = [round(t["plans_symbolic_ms"], 1) for t in splits]
+    split["per_step_copy_ms"] = [round(t["copy_ms"], 1) for t in splits]
     return {"value": round(2.0 * fl / sec / 1e9, 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": round(sec * 1e3, 3), "steps": nsteps, "split": split,

@@ -224,7 +224,7 @@ __device__ __forceinline__ void chain_num_bin(const ChainProduct& c, IT* colC, V
 
 template <class IT, class V>
 __global__ void __launch_bounds__(kChainThreads, 1)
-    chain_kernel(const ChainProduct* __restrict__ steps, ChainSync* sync) {
+    chain_kernel(const ChainProduct* __restrict__ steps, ChainSync* sync, int sym_groups) {
     const long long bid = blockIdx.x, nb = gridDim.x;
     const int nsteps = sync->nsteps;
     if (bid == 0 && threadIdx.x == 0 && sync->stamps) sync->stamps[0] = globaltimer_ns();
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         }
         symbolic_dense_kernel_body<IT, kChainThreads, 1>(
             c.D, c.rb, c.nprod, c.rows, c.cnt, c.max_words, c.W / 32, c.chunkcnt, c.rowptrC,
-            &c.cnt->work_counter[0], err, bid, nb);
+            &c.cnt->work_counter[0], err, bid, nb, sym_groups);
         if (!chain_barrier(sync, stage++)) return;
         // row pointers: exclusive scan of the counts (R + 1 entries)
         chain_scan_sums(c.rowptrC, c.R + 1, c.scan, bid, nb);
@@ -314,6 +314,14 @@ cudaError_t launch_chain(const ChainProduct* steps, ChainSync* sync, int max_wor
                          cudaStream_t s, int* grid_out) {
     auto k = chain_kernel<IT, V>;
     const size_t smem = chain_smem_bytes<IT, V>(max_words);
+    // the dense symbolic stage runs one row per group of warps, as many
+    // groups as their bitmaps fit the block's shared memory (at most 6)
+    int sym_groups = 1;
+    for (int gg : {6, 4, 3, 2})
+        if ((size_t)gg * (size_t)max_words * 4 <= smem) {
+            sym_groups = gg;
+            break;
+        }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -324,7 +332,7 @@ cudaError_t launch_chain(const ChainProduct* steps, ChainSync* sync, int max_wor
     if (grid_out) *grid_out = grid;
     if ((e = cudaMemsetAsync(sync, 0, 16, s)) != cudaSuccess) return e;
     count_launches(1);
-    k<<<grid, kChainThreads, smem, s>>>(steps, sync);
+    k<<<grid, kChainThreads, smem, s>>>(steps, sync, sym_groups);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,21 @@ __device__ __forceinline__ RowCtx<IT, V> row_ctx(const ProdDesc* __restrict__ D,
     return c;
 }
 
+// The rows rows[first], rows[first + stride], ... (< nrows) of a class,
+// walked by one warp.  (Loading the next rows' ids and bounds while a row is
+// processed was measured on the short rows of the AMG hierarchy and gained
+// nothing.)
+template <class IT, class V, class F>
+__device__ __forceinline__ void for_class_rows(const ProdDesc* __restrict__ D,
+                                               const long long* __restrict__ rb, int nprod,
+                                               const int32_t* __restrict__ crow, long long first,
+                                               long long nrows, long long stride, F&& f) {
+    for (long long rr = first; rr < nrows; rr += stride) {
+        const long long r = crow[rr];
+        f(row_ctx<IT, V>(D, rb, nprod, r), r);
+    }
+}
+
 // Rows [r0, r1) of a block by class: with base == nullptr, count them per
 // class into loc; else place row r at base[c] + a slot taken from loc[c].
 // Lanes of a warp with the same class take one atomic together.
@@ -230,7 +245,70 @@ __device__ __forceinline__ void analyze_kernel_body(long long R, const ProdDesc*
     const long long warp = ((long long)vbid * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)vnb * blockDim.x) >> 5;
     unsigned long long my_total = 0, my_max = 0;
-    for (long long r = warp; r < R; r += nwarps) {
+    if (!prm) {
+        // Tiles of 32 rows: a row of at most 32 A entries is summed by its
+        // own lane (eight entries' loads in flight at a time); longer rows
+        // by the whole warp, one after another.
+        for (long long tile = warp; tile * 32 < R; tile += nwarps) {
+            const long long r = tile * 32 + lane;
+            const bool in = r < R;
+            RowCtx<IT, NoVal> c{};
+            if (in) c = row_ctx<IT, NoVal>(D, rb, nprod, r);
+            const long long d = in ? c.a1 - c.a0 : 0;
+            long long f = 0, mx = 0;
+            if (in && d <= 32) {
+                for (long long p0 = c.a0; p0 < c.a1; p0 += 8) {
+                    long long k[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) k[u] = p0 + u < c.a1 ? (long long)c.ciA[p0 + u] : -1;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (k[u] >= 0) {
+                            const long long len = c.rpB[k[u] + 1] - c.rpB[k[u]];
+                            f += len;
+                            mx = len > mx ? len : mx;
+                        }
+                    }
+                }
+            }
+            for (unsigned lm = __ballot_sync(kFull, in && d > 32); lm; lm &= lm - 1u) {
+                const int src = __ffs(lm) - 1;
+                const RowCtx<IT, NoVal> cs = row_ctx<IT, NoVal>(D, rb, nprod, tile * 32 + src);
+                long long fs = 0, ms = 0;
+                for (long long p = cs.a0 + lane; p < cs.a1; p += 32) {
+                    const long long k = (long long)cs.ciA[p];
+                    const long long len = cs.rpB[k + 1] - cs.rpB[k];
+                    fs += len;
+                    ms = len > ms ? len : ms;
+                }
+                fs = warp_sum(fs);
+                ms = warp_max(ms);
+                if (lane == src) {
+                    f = fs;
+                    mx = ms;
+                }
+            }
+            int cl = -1 - lane;
+            if (in) {
+                flops_out[r] = f;
+                if (cap_out) cap_out[r] = f;
+                cl = row_class(f, dense_min, hash_shift);
+                cls_out[r] = (unsigned char)cl;
+                if (cl >= kClassDense0) {
+                    if (c.n > max_dense_n) blk_unsup = 1;
+                    atomicMax(&blk_dlen, (unsigned long long)d);
+                }
+                my_total += (unsigned long long)f;
+                if ((unsigned long long)f > my_max) my_max = (unsigned long long)f;
+            }
+            // one shared atomic per class present in the tile
+            const unsigned grp = __match_any_sync(kFull, cl);
+            if (in && (grp & lanemask_lt()) == 0u) atomicAdd(&hist[cl], (unsigned long long)__popc(grp));
+        }
+        my_total = warp_sum(my_total);
+        my_max = warp_max(my_max);
+    }
+    for (long long r = prm ? warp : R; r < R; r += nwarps) {
         const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
         long long f = 0, mx = 0;
         for (long long p = c.a0 + lane; p < c.a1; p += 32) {
@@ -461,6 +539,9 @@ __device__ __forceinline__ void short_row_numeric(const RowCtx<IT, V>& c, long l
     using K = typename KeyT<IT>::type;
     constexpr bool HV = VOps<V>::has_val;
     const int lane = lane_id();
+    // the output range does not depend on the products: loaded first
+    const long long out = rpC[r];
+    long long rcnt = rpC[r + 1] - out;
     K key;
     V v;
     const int np = short_row_gather<IT, V, HV>(c, key, v);
@@ -492,8 +573,6 @@ __device__ __forceinline__ void short_row_numeric(const RowCtx<IT, V>& c, long l
         const K kj = __shfl_sync(kFull, kk, __ffs(Lr) - 1);
         pos += kj < kk ? 1 : 0;
     }
-    const long long out = rpC[r];
-    long long rcnt = rpC[r + 1] - out;
     if (rowend != nullptr) {
         if (cnt > rcnt) {
             if (lane == 0) {
@@ -533,10 +612,10 @@ __device__ __forceinline__ void symbolic_hash_kernel_body(
     const long long nw = (long long)vnb * WARPS;
     if constexpr (LOG2T == kShortLog2T) {
         // rows of at most 32 products: no table
-        for (long long rr = gw; rr < nrows; rr += nw) {
-            const long long r = crow[rr];
-            short_row_symbolic<IT>(row_ctx<IT, NoVal>(D, rb, nprod, r), r, rowcnt, err);
-        }
+        for_class_rows<IT, NoVal>(D, rb, nprod, crow, gw, nrows, nw,
+                                  [&](const RowCtx<IT, NoVal>& c, long long r) {
+                                      short_row_symbolic<IT>(c, r, rowcnt, err);
+                                  });
         return;
     }
     K* keys = reinterpret_cast<K*>(smem_raw) + (size_t)w * T;
@@ -595,6 +674,17 @@ __global__ void __launch_bounds__(WARPS * 32)
 // MAXT / MINB: launch bounds of the instantiation (a register cap that lets
 // six 256-thread or three 512-thread blocks share an SM, or one 1024-thread
 // block for a bitmap that leaves room for only one block).
+// Groups: the block may be split into `groups` equal groups of whole warps
+// (named barriers 1..groups), each with its own bitmap of max_words words,
+// so that several rows are in flight in one block; groups == 1 is the
+// whole block.
+constexpr int kMaxSymGroups = 8;
+
+__device__ __forceinline__ void group_sync(int g, int gthreads, int groups) {
+    if (groups == 1) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(gthreads) : "memory");
+}
+
 template <class IT, int MAXT, int MINB>
 __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __restrict__ D,
                                       const long long* __restrict__ rb, int nprod,
@@ -602,23 +692,29 @@ __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __res
                                       int max_words, int chunk_words,
                                       int32_t* __restrict__ chunkcnt, int64_t* __restrict__ rowcnt,
                                       unsigned long long* work, int* err,
-        const long long vbid, const long long vnb) {
-    extern __shared__ unsigned bm[];
-    __shared__ long long row_total;
-    __shared__ long long cur_row;
+        const long long vbid, const long long vnb, const int groups = 1) {
+    extern __shared__ unsigned bm_all[];
+    __shared__ long long row_total_g[kMaxSymGroups];
+    __shared__ long long cur_row_g[kMaxSymGroups];
+    const int gthreads = blockDim.x / groups;
+    const int g = threadIdx.x / gthreads;
+    const int gt = threadIdx.x - g * gthreads;
+    unsigned* bm = bm_all + (size_t)g * max_words;
+    long long& row_total = row_total_g[g];
+    long long& cur_row = cur_row_g[g];
     const int lane = lane_id();
-    const int w = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int w = gt >> 5;
+    const int nwarps = gthreads >> 5;
     unsigned long long nd = 0;
     for (int t = kClassDense0; t < kNumClasses; ++t) nd += cnt->class_count[t];
     const long long nrows = (long long)nd;
     const int32_t* drow = rows + cnt->class_off[kClassDense0];
-    for (int t = threadIdx.x; t < max_words; t += blockDim.x) bm[t] = 0u;
-    if (threadIdx.x == 0) row_total = 0;
-    __syncthreads();
+    for (int t = gt; t < max_words; t += gthreads) bm[t] = 0u;
+    if (gt == 0) row_total = 0;
+    group_sync(g, gthreads, groups);
     while (true) {
-        if (threadIdx.x == 0) cur_row = (long long)atomicAdd(work, 1ull);
-        __syncthreads();
+        if (gt == 0) cur_row = (long long)atomicAdd(work, 1ull);
+        group_sync(g, gthreads, groups);
         const long long rr = cur_row;
         if (rr >= nrows) break;
         const long long r = drow[rr];
@@ -630,8 +726,8 @@ __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __res
         const int NW = (int)((cx.n + 31) >> 5);
         const int P = cx.P;
         if (NW > max_words) {  // n beyond the shared-memory bitmap: reported, row skipped
-            if (threadIdx.x == 0) atomicExch(err, (int)kDevTooWide);
-            __syncthreads();
+            if (gt == 0) atomicExch(err, (int)kDevTooWide);
+            group_sync(g, gthreads, groups);
             continue;
         }
         for (long long b = a0 + (long long)w * 32; b < a1; b += (long long)nwarps * 32) {
@@ -653,7 +749,7 @@ __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __res
                     if (j[t] >= 0) atomicOr(&bm[j[t] >> 5], 1u << (j[t] & 31));
             });
         }
-        __syncthreads();
+        group_sync(g, gthreads, groups);
         long long part = 0;
         for (int c = w; c < P; c += nwarps) {
             const int w0 = c * chunk_words;
@@ -668,12 +764,12 @@ __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __res
             part += s;
         }
         if (lane == 0 && part) atomicAdd((unsigned long long*)&row_total, (unsigned long long)part);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        group_sync(g, gthreads, groups);
+        if (gt == 0) {
             rowcnt[r] = row_total;
             row_total = 0;
         }
-        __syncthreads();
+        group_sync(g, gthreads, groups);
     }
 }
 
@@ -797,11 +893,11 @@ __device__ __forceinline__ void numeric_hash_kernel_body(
         const int32_t* crow = rows + cnt->class_off[cls];
         const long long gw = (long long)vbid * WARPS + w;
         const long long nw = (long long)vnb * WARPS;
-        for (long long rr = gw; rr < nrows; rr += nw) {
-            const long long r = crow[rr];
-            short_row_numeric<IT, V>(row_ctx<IT, V>(D, rb, nprod, r), r, rpC, cap, ciC, vC, err,
-                                     rowend, overflow, overflow_count);
-        }
+        for_class_rows<IT, V>(D, rb, nprod, crow, gw, nrows, nw,
+                              [&](const RowCtx<IT, V>& c, long long r) {
+                                  short_row_numeric<IT, V>(c, r, rpC, cap, ciC, vC, err, rowend,
+                                                           overflow, overflow_count);
+                              });
         return;
     }
     // layout per warp: T values (if any), T keys, 256 radix counters
