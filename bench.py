@@ -642,6 +642,18 @@ def run_mcl(args, sg, torch, params, margin):
                     "compared panels' plain products"}
 
 
+def _anon_huge_bytes():
+    """Bytes of this process's anonymous memory held in transparent huge
+    pages (the pinned host buffers of the end-to-end leg ask for them)."""
+    try:
+        for ln in open("/proc/self/smaps_rollup"):
+            if ln.startswith("AnonHugePages:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def run_e2e(args, A, sg, torch, dev, dP):
     """Same metric through the public API from pinned host buffers: H2D of
     A, then C = A.A delivered to pinned host memory by row panels whose
@@ -698,6 +710,8 @@ def run_e2e(args, A, sg, torch, dev, dP):
                        "first_numeric_to_last_copy_ms", "wall_ms")}
     split["h2d_gbs"] = round(h2d / (split["h2d_ms"] * 1e-3) / 1e9, 1)
     split["d2h_gbs"] = round(last["d2h_bytes"] / (split["copy_ms"] * 1e-3) / 1e9, 1)
+    split["host_huge_page_bytes"] = _anon_huge_bytes()
+    split["host_buffer_bytes"] = int(h2d + d2h)
     split["per_step_wall_ms"] = [round(t["wall_ms"], 1) for t in splits]
     split["per_step_plans_symbolic_ms"] = [round(t["plans_symbolic_ms"], 1) for t in splits]
     split["per_step_copy_ms"] = [round(t["copy_ms"], 1) for t in splits]

@@ -186,8 +186,11 @@ __device__ __forceinline__ void chain_zero_rows(const ChainProduct& c, long long
 
 // Warps of the persistent block that run a hash bin with tables of 2^LOG2T
 // slots: all of them while their tables fit the shared-memory budget, else
-// half, a quarter or an eighth (the others wait at the stage's end).
-constexpr size_t kChainSmemBudget = 208 * 1024;
+// half, a quarter or an eighth (the others wait at the stage's end).  The
+// budget is what a block may hold on sm_103 (227 KB) less the kernel's own
+// static arrays (under 8 KB); it lets 24 warps hold float32 tables of 1024
+// slots.
+constexpr size_t kChainSmemBudget = 216 * 1024;
 template <class K, class V, int LOG2T, bool NUMERIC>
 constexpr int chain_bin_warps() {
     constexpr size_t vb = NUMERIC && VOps<V>::has_val ? sizeof(V) : 0;
