@@ -703,6 +703,19 @@ def run_e2e(args, A, sg, torch, dev, dP):
         del M
     fl = sg.plan(sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv),
                  sg.DeviceCSR(A.nrows, A.ncols, dr, dc, dv)).info()["flops"]
+    # the link by itself at this moment: one 2 GiB device-to-host copy into
+    # the same host buffer, outside the timed steps
+    probe = torch.empty(1 << 28, dtype=torch.float64, device=dev)
+    probe.fill_(1.0)
+    ms_link = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out_host.val[:probe.numel()].copy_(probe, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        ms_link.append(a.elapsed_time(b))
+    del probe
     sec = float(np.mean(times))
     last = splits[-1]
     split = {k: round(float(np.mean([t[k] for t in splits])), 3)
@@ -710,6 +723,7 @@ def run_e2e(args, A, sg, torch, dev, dP):
                        "first_numeric_to_last_copy_ms", "wall_ms")}
     split["h2d_gbs"] = round(h2d / (split["h2d_ms"] * 1e-3) / 1e9, 1)
     split["d2h_gbs"] = round(last["d2h_bytes"] / (split["copy_ms"] * 1e-3) / 1e9, 1)
+    split["link_d2h_gbs"] = round((1 << 31) / (min(ms_link) * 1e-3) / 1e9, 1)
     split["host_huge_page_bytes"] = _anon_huge_bytes()
     split["host_buffer_bytes"] = int(h2d + d2h)
     split["per_step_wall_ms"] = [round(t["wall_ms"], 1) for t in splits]

@@ -234,7 +234,11 @@ typedef struct {
 typedef struct {
     double timeout_s;       /* bound of every barrier wait; 0 = 10 s */
     int32_t withhold_stage; /* -1, or a stage whose completion is withheld (tests) */
-    int32_t reserved;
+    /* threads of a persistent block: 0 or 768 (24 warps of up to 80
+     * registers; the dense numeric stage needs them), or 1024 (32 warps of up
+     * to 64 registers: more rows in flight for chains of short rows, such as
+     * the levels of a Galerkin hierarchy); INVALID_ARG otherwise */
+    int32_t block_threads;
     /* NULL, or a device array of 2 + 6 * nsteps uint64 that every launch
      * fills with %globaltimer readings (ns) of block 0: [0] at its start,
      * [1 + s] when it passed the barrier after stage s (stage 0 clears the

@@ -68,7 +68,10 @@ class GalerkinChain:
             for lv in self.levels:
                 steps.append((lv["p1"], lv["T"].rowptr, lv["cap"], lv["T"].col, lv["T"].val))
                 steps.append((lv["p2"], lv["A"].rowptr, lv["cap"], lv["A"].col, lv["A"].val))
-            self.chain = sg.Chain(steps, timeout_s=timeout_s, record_stages=record_stages)
+            # the hierarchy's rows are short (at most 56 products on a 7-point
+            # stencil): 1024-thread blocks keep more of them in flight
+            self.chain = sg.Chain(steps, timeout_s=timeout_s, record_stages=record_stages,
+                                  block_threads=1024)
 
     def _transpose(self, lv):
         Rt = lv["Rt"]

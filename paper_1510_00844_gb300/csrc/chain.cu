@@ -8,7 +8,7 @@
 #include "chain.h"
 
 struct spgemm_chain_s {
-    int it = 0, vt = 0, nsteps = 0, max_words = 1, sm_count = 1;
+    int it = 0, vt = 0, nsteps = 0, max_words = 1, sm_count = 1, threads = 768;
     sg::ChainSync* sync = nullptr;          // in the caller's chain workspace
     sg::ChainProduct* steps = nullptr;
     int grid = 0;
@@ -69,6 +69,9 @@ spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps
     spgemm_chain_opts o{};
     if (opts) o = *opts;
     if (o.timeout_s < 0) return chain_fail(SPGEMM_ERR_INVALID_ARG, "negative timeout");
+    if (o.block_threads != 0 && o.block_threads != sg::kChainThreads &&
+        o.block_threads != sg::kChainThreadsWide)
+        return chain_fail(SPGEMM_ERR_INVALID_ARG, "block_threads must be 0, 768 or 1024");
     const spgemm_plan_t P0 = steps[0].plan;
     if (!P0) return chain_fail(SPGEMM_ERR_INVALID_ARG, "step 0 has no plan");
     if (!chain_value_kind(P0->vt))
@@ -122,7 +125,7 @@ spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps
         max_words = std::max(max_words, (std::min(P->max_n, P->max_dense_n) + 31) / 32);
         // the dense stages use 8 warps per persistent block; their cursor
         // arena slots must exist in the plan's workspace
-        const int dense_warps = P->W == sg::kDenseW0 ? sg::kChainWarps : sg::kChainHalf;
+        const int dense_warps = P->W == sg::kDenseW0 ? sg::kChainDense0 : sg::kChainDense1;
         if (P->dense_grid * P->dense_warps_per_block < (long long)P->sm_count * dense_warps)
             return chain_fail(SPGEMM_ERR_NOT_SUPPORTED, "plan's dense arena too small for a chain");
     }
@@ -144,6 +147,7 @@ spgemm_status spgemm_chain_create(int32_t nsteps, const spgemm_chain_step* steps
     C->nsteps = nsteps;
     C->max_words = (int)max_words;
     C->sm_count = sms;
+    C->threads = o.block_threads ? o.block_threads : sg::kChainThreads;
     unsigned char* base = (unsigned char*)chain_ws;
     C->sync = (sg::ChainSync*)base;
     C->steps = (sg::ChainProduct*)(base + align_up(sizeof(sg::ChainSync)));
@@ -171,7 +175,11 @@ spgemm_status spgemm_chain_launch(spgemm_chain_t C, void* stream) {
     cudaError_t e = with_chain_types(C->it, C->vt, [&](auto itag, auto vtag) -> cudaError_t {
         using IT = decltype(itag);
         using V = decltype(vtag);
-        return sg::launch_chain<IT, V>(C->steps, C->sync, C->max_words, C->sm_count, s, &C->grid);
+        if (C->threads == sg::kChainThreadsWide)
+            return sg::launch_chain<IT, V, sg::kChainThreadsWide>(C->steps, C->sync, C->max_words,
+                                                                  C->sm_count, s, &C->grid);
+        return sg::launch_chain<IT, V, sg::kChainThreads>(C->steps, C->sync, C->max_words,
+                                                          C->sm_count, s, &C->grid);
     });
     if (e != cudaSuccess) return chain_cuda_fail(e, "chain launch");
     return SPGEMM_OK;

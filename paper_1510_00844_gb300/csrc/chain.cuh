@@ -116,7 +116,7 @@ __device__ __forceinline__ void chain_bin(const ChainProduct& c, long long bid, 
 // Row-pointer scan, first stage: sums of tiles of kScanTile entries.
 __device__ __forceinline__ void chain_scan_sums(const int64_t* x, long long N, int64_t* part,
                                                 long long bid, long long nb) {
-    __shared__ long long ws[kChainWarps];
+    __shared__ long long ws[kChainMaxWarps];
     const long long ntiles = (N + kScanTile - 1) / kScanTile;
     for (long long tile = bid; tile < ntiles; tile += nb) {
         long long s = 0;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void chain_scan_sums(const int64_t* x, long long N, i
         if (lane_id() == 0) ws[threadIdx.x >> 5] = s;
         __syncthreads();
         if (threadIdx.x < 32) {
-            long long v = threadIdx.x < kChainWarps ? ws[threadIdx.x] : 0;
+            long long v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
             v = warp_sum(v);
             if (threadIdx.x == 0) part[tile] = v;
         }
@@ -139,7 +139,7 @@ __device__ __forceinline__ void chain_scan_sums(const int64_t* x, long long N, i
 // block itself) and scans its entries in place (exclusive).
 __device__ __forceinline__ void chain_scan_apply(int64_t* x, long long N, const int64_t* part,
                                                  long long bid, long long nb) {
-    __shared__ long long ws[kChainWarps];
+    __shared__ long long ws[kChainMaxWarps];
     __shared__ long long carry;
     const long long ntiles = (N + kScanTile - 1) / kScanTile;
     for (long long tile = bid; tile < ntiles; tile += nb) {
@@ -150,7 +150,7 @@ __device__ __forceinline__ void chain_scan_apply(int64_t* x, long long N, const 
         __syncthreads();
         if (threadIdx.x == 0) {
             long long t = 0;
-            for (int w = 0; w < kChainWarps; ++w) t += ws[w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
             carry = t;
         }
         __syncthreads();
@@ -162,9 +162,9 @@ __device__ __forceinline__ void chain_scan_apply(int64_t* x, long long N, const 
             if (lane_id() == 31) ws[threadIdx.x >> 5] = inc;
             __syncthreads();
             if (threadIdx.x < 32) {
-                const long long w = threadIdx.x < kChainWarps ? ws[threadIdx.x] : 0;
+                const long long w = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
                 const long long wi = warp_incl_scan(w);
-                if (threadIdx.x < kChainWarps) ws[threadIdx.x] = wi - w;
+                if (threadIdx.x < (blockDim.x >> 5)) ws[threadIdx.x] = wi - w;
             }
             __syncthreads();
             const long long excl = carry + ws[threadIdx.x >> 5] + inc - v;
@@ -184,28 +184,24 @@ __device__ __forceinline__ void chain_zero_rows(const ChainProduct& c, long long
         c.rowptrC[erow[r]] = 0;
 }
 
-// Warps of the persistent block that run a hash bin with tables of 2^LOG2T
-// slots: all of them while their tables fit the shared-memory budget, else
-// half, a quarter or an eighth (the others wait at the stage's end).  The
-// budget is what a block may hold on sm_103 (227 KB) less the kernel's own
-// static arrays (under 8 KB); it lets 24 warps hold float32 tables of 1024
-// slots.
+// Warps of a persistent block of BW warps that run a hash bin with tables
+// of 2^LOG2T slots: as many as their tables fit in the shared-memory budget
+// (the others wait at the stage's end).  The budget is what a block may hold
+// on sm_103 (227 KB) less the kernel's own static arrays (under 8 KB); it
+// lets 24 warps hold float32 tables of 1024 slots.
 constexpr size_t kChainSmemBudget = 216 * 1024;
-template <class K, class V, int LOG2T, bool NUMERIC>
+template <class K, class V, int LOG2T, bool NUMERIC, int BW>
 constexpr int chain_bin_warps() {
     constexpr size_t vb = NUMERIC && VOps<V>::has_val ? sizeof(V) : 0;
     constexpr size_t per = (size_t(1) << LOG2T) * (sizeof(K) + vb) + (NUMERIC ? 1024 : 0);
-    return kChainWarps * per <= kChainSmemBudget       ? kChainWarps
-           : (kChainWarps / 2) * per <= kChainSmemBudget ? kChainWarps / 2
-           : (kChainWarps / 4) * per <= kChainSmemBudget ? kChainWarps / 4
-                                                          : kChainWarps / 8;
+    return (int)(kChainSmemBudget / per) >= BW ? BW : (int)(kChainSmemBudget / per);
 }
 
 // One hash bin of the symbolic / numeric stage on the warps its tables allow.
-template <class IT, class K, int LOG2T>
+template <class IT, class K, int LOG2T, int BW>
 __device__ __forceinline__ void chain_sym_bin(const ChainProduct& c, int* err, long long bid,
                                               long long nb) {
-    constexpr int WARPS = chain_bin_warps<K, NoVal, LOG2T, false>();
+    constexpr int WARPS = chain_bin_warps<K, NoVal, LOG2T, false, BW>();
     const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
     if (threadIdx.x < WARPS * 32)
         symbolic_hash_kernel_body<IT, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
@@ -213,10 +209,10 @@ __device__ __forceinline__ void chain_sym_bin(const ChainProduct& c, int* err, l
     __syncthreads();
 }
 
-template <class IT, class V, class K, int LOG2T>
+template <class IT, class V, class K, int LOG2T, int BW>
 __device__ __forceinline__ void chain_num_bin(const ChainProduct& c, IT* colC, V* valC, int* err,
                                               long long bid, long long nb) {
-    constexpr int WARPS = chain_bin_warps<K, V, LOG2T, true>();
+    constexpr int WARPS = chain_bin_warps<K, V, LOG2T, true, BW>();
     const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
     if (threadIdx.x < WARPS * 32)
         numeric_hash_kernel_body<IT, V, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
@@ -225,9 +221,10 @@ __device__ __forceinline__ void chain_num_bin(const ChainProduct& c, IT* colC, V
     __syncthreads();
 }
 
-template <class IT, class V>
-__global__ void __launch_bounds__(kChainThreads, 1)
+template <class IT, class V, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
     chain_kernel(const ChainProduct* __restrict__ steps, ChainSync* sync, int sym_groups) {
+    constexpr int BW = THREADS / 32;
     const long long bid = blockIdx.x, nb = gridDim.x;
     const int nsteps = sync->nsteps;
     if (bid == 0 && threadIdx.x == 0 && sync->stamps) sync->stamps[0] = globaltimer_ns();
@@ -252,16 +249,16 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         // symbolic phase: row counts into rowptrC
         chain_zero_rows(c, bid, nb);
         using K = typename KeyT<IT>::type;
-        chain_sym_bin<IT, K, 6>(c, err, bid, nb);
-        chain_sym_bin<IT, K, 8>(c, err, bid, nb);
-        chain_sym_bin<IT, K, 10>(c, err, bid, nb);
-        chain_sym_bin<IT, K, 11>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 6, BW>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 8, BW>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 10, BW>(c, err, bid, nb);
+        chain_sym_bin<IT, K, 11, BW>(c, err, bid, nb);
         if (c.LB > 0) {
             segtab_kernel_body<IT>(c.LB, c.D, c.bb, c.nprod, c.W, c.segtab, c.cnt, bid, nb);
             runlen_kernel_body<IT>(c.LB, c.D, c.bb, c.nprod, c.W, c.runlen, c.nextrun, c.cnt, bid,
                                    nb);
         }
-        symbolic_dense_kernel_body<IT, kChainThreads, 1>(
+        symbolic_dense_kernel_body<IT, THREADS, 1>(
             c.D, c.rb, c.nprod, c.rows, c.cnt, c.max_words, c.W / 32, c.chunkcnt, c.rowptrC,
             &c.cnt->work_counter[0], err, bid, nb, sym_groups);
         if (!chain_barrier(sync, stage++)) return;
@@ -273,27 +270,30 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         // numeric phase
         IT* colC = (IT*)c.colC;
         V* valC = (V*)c.valC;
-        chain_num_bin<IT, V, K, 6>(c, colC, valC, err, bid, nb);
-        chain_num_bin<IT, V, K, 8>(c, colC, valC, err, bid, nb);
-        chain_num_bin<IT, V, K, 10>(c, colC, valC, err, bid, nb);
-        chain_num_bin<IT, V, K, 11>(c, colC, valC, err, bid, nb);
-        if (c.W == kDenseW0)
-            numeric_dense_kernel_body<IT, V, kDenseW0, kChainWarps>(
+        chain_num_bin<IT, V, K, 6, BW>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 8, BW>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 10, BW>(c, colC, valC, err, bid, nb);
+        chain_num_bin<IT, V, K, 11, BW>(c, colC, valC, err, bid, nb);
+        if (c.W == kDenseW0) {
+            if (threadIdx.x < kChainDense0 * 32)
+                numeric_dense_kernel_body<IT, V, kDenseW0, kChainDense0>(
                 c.D, c.rb, c.nprod, c.rows, c.cnt, c.chunkcnt, c.segtab, c.runlen, c.nextrun,
                 c.arena, c.arena_stride, c.rowptrC, c.capacity, colC, valC, c.max_dense_n,
                 &c.cnt->work_counter[1], err, nullptr, nullptr, nullptr, nullptr, bid, nb);
-        else if (threadIdx.x < kChainHalf * 32)
-            numeric_dense_kernel_body<IT, V, kDenseW1, kChainHalf>(
+        } else if (threadIdx.x < kChainDense1 * 32) {
+            numeric_dense_kernel_body<IT, V, kDenseW1, kChainDense1>(
                 c.D, c.rb, c.nprod, c.rows, c.cnt, c.chunkcnt, c.segtab, c.runlen, c.nextrun,
                 c.arena, c.arena_stride, c.rowptrC, c.capacity, colC, valC, c.max_dense_n,
                 &c.cnt->work_counter[1], err, nullptr, nullptr, nullptr, nullptr, bid, nb);
+        }
         if (!chain_barrier(sync, stage++)) return;
     }
 }
 
 // Shared memory of the persistent block: the largest stage of the chain.
-template <class IT, class V>
+template <class IT, class V, int THREADS>
 size_t chain_smem_bytes(int max_words) {
+    constexpr int BW = THREADS / 32;
     using K = typename KeyT<IT>::type;
     constexpr size_t vb = VOps<V>::has_val ? sizeof(V) : 0;
     auto bin = [&](int log2t, int warps, bool numeric) {
@@ -301,41 +301,42 @@ size_t chain_smem_bytes(int max_words) {
                                 (numeric ? 1024 : 0));
     };
     size_t b = 0;
-    b = std::max(b, bin(10, chain_bin_warps<K, NoVal, 10, false>(), false));
-    b = std::max(b, bin(11, chain_bin_warps<K, NoVal, 11, false>(), false));
-    b = std::max(b, bin(8, chain_bin_warps<K, V, 8, true>(), true));
-    b = std::max(b, bin(10, chain_bin_warps<K, V, 10, true>(), true));
-    b = std::max(b, bin(11, chain_bin_warps<K, V, 11, true>(), true));
-    b = std::max(b, (size_t)kChainWarps * ((vb * kDenseW0) + kDenseW0 / 8 + 32 * sizeof(DenseRun<V>)));
-    b = std::max(b, (size_t)kChainHalf * ((vb * kDenseW1) + kDenseW1 / 8 + 32 * sizeof(DenseRun<V>)));
+    b = std::max(b, bin(10, chain_bin_warps<K, NoVal, 10, false, BW>(), false));
+    b = std::max(b, bin(11, chain_bin_warps<K, NoVal, 11, false, BW>(), false));
+    b = std::max(b, bin(8, chain_bin_warps<K, V, 8, true, BW>(), true));
+    b = std::max(b, bin(10, chain_bin_warps<K, V, 10, true, BW>(), true));
+    b = std::max(b, bin(11, chain_bin_warps<K, V, 11, true, BW>(), true));
+    b = std::max(b, (size_t)kChainDense0 * ((vb * kDenseW0) + kDenseW0 / 8 + 32 * sizeof(DenseRun<V>)));
+    b = std::max(b, (size_t)kChainDense1 * ((vb * kDenseW1) + kDenseW1 / 8 + 32 * sizeof(DenseRun<V>)));
     b = std::max(b, (size_t)max_words * 4);                                         // dense symbolic
     return b;
 }
 
-template <class IT, class V>
+template <class IT, class V, int THREADS>
 cudaError_t launch_chain(const ChainProduct* steps, ChainSync* sync, int max_words, int sm_count,
                          cudaStream_t s, int* grid_out) {
-    auto k = chain_kernel<IT, V>;
-    const size_t smem = chain_smem_bytes<IT, V>(max_words);
-    // the dense symbolic stage runs one row per group of warps, as many
-    // groups as their bitmaps fit the block's shared memory (at most 6)
+    auto k = chain_kernel<IT, V, THREADS>;
+    const size_t smem = chain_smem_bytes<IT, V, THREADS>(max_words);
+    // the dense symbolic stage runs one row per group of at least four
+    // warps, as many groups as their bitmaps fit the block's shared memory
     int sym_groups = 1;
-    for (int gg : {6, 4, 3, 2})
-        if ((size_t)gg * (size_t)max_words * 4 <= smem) {
+    for (int gg : {8, 6, 4, 3, 2})
+        if ((THREADS / 32) % gg == 0 && THREADS / 32 / gg >= 4 &&
+            (size_t)gg * (size_t)max_words * 4 <= smem) {
             sym_groups = gg;
             break;
         }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kChainThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, THREADS, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int grid = sm_count * occ;
     if (grid_out) *grid_out = grid;
     if ((e = cudaMemsetAsync(sync, 0, 16, s)) != cudaSuccess) return e;
     count_launches(1);
-    k<<<grid, kChainThreads, smem, s>>>(steps, sync, sym_groups);
+    k<<<grid, THREADS, smem, s>>>(steps, sync, sym_groups);
     return cudaGetLastError();
 }
 

@@ -7,12 +7,16 @@
 
 namespace sg {
 
-constexpr int kChainThreads = 768;   // 24 warps per persistent block
-constexpr int kChainWarps = kChainThreads / 32;
-// Warps of the persistent block that run a stage whose per-warp shared
-// memory would not fit 16 times (the largest hash bins, wide dense chunks);
-// the other warps wait at the stage's end.
-constexpr int kChainHalf = kChainWarps / 2;
+// Threads of a persistent block: 768 (24 warps at up to 80 registers, what
+// the dense numeric stage needs), or 1024 (32 warps at up to 64 registers,
+// for chains of short rows whose stages wait on memory latency).
+constexpr int kChainThreads = 768;
+constexpr int kChainThreadsWide = 1024;
+constexpr int kChainMaxWarps = kChainThreadsWide / 32;
+// Warps that run the dense numeric stage: 1024-column chunks on 24 warps,
+// 2048-column chunks on 12 (their accumulators fill the shared memory).
+constexpr int kChainDense0 = 24;
+constexpr int kChainDense1 = 12;
 constexpr int kDevTimeout = 8;       // a chain barrier wait expired
 
 // One product of a chain: everything its stages read, from a device-sized
@@ -54,9 +58,9 @@ struct ChainSync {
     unsigned long long* stamps;  // NULL, or 2 + 6 * nsteps %globaltimer readings
 };
 
-template <class IT, class V>
+template <class IT, class V, int THREADS>
 size_t chain_smem_bytes(int max_words);
-template <class IT, class V>
+template <class IT, class V, int THREADS>
 cudaError_t launch_chain(const ChainProduct* steps, ChainSync* sync, int max_words, int sm_count,
                          cudaStream_t s, int* grid_out);
 

@@ -5,7 +5,7 @@
 #include "plan.h"
 #include "chain.cuh"
 
-#define SG_INSTANTIATE_CHAIN(IT, V)                                                              \
-    template cudaError_t launch_chain<IT, V>(const ChainProduct*, ChainSync*, int, int,         \
-                                             cudaStream_t, int*);                                \
-    template size_t chain_smem_bytes<IT, V>(int);
+#define SG_INSTANTIATE_CHAIN(IT, V, THREADS)                                                     \
+    template cudaError_t launch_chain<IT, V, THREADS>(const ChainProduct*, ChainSync*, int, int, \
+                                                      cudaStream_t, int*);                       \
+    template size_t chain_smem_bytes<IT, V, THREADS>(int);

@@ -3,6 +3,6 @@
 #include "chain_launch.h"
 
 namespace sg {
-SG_INSTANTIATE_CHAIN(int32_t, double)
-SG_INSTANTIATE_CHAIN(int32_t, float)
+SG_INSTANTIATE_CHAIN(int32_t, double, kChainThreads)
+SG_INSTANTIATE_CHAIN(int32_t, float, kChainThreads)
 }  // namespace sg

@@ -3,6 +3,6 @@
 #include "chain_launch.h"
 
 namespace sg {
-SG_INSTANTIATE_CHAIN(int32_t, int64_t)
-SG_INSTANTIATE_CHAIN(int32_t, NoVal)
+SG_INSTANTIATE_CHAIN(int32_t, int64_t, kChainThreads)
+SG_INSTANTIATE_CHAIN(int32_t, NoVal, kChainThreads)
 }  // namespace sg

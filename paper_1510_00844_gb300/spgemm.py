@@ -338,7 +338,7 @@ class _ChainStep(ctypes.Structure):
 
 class _ChainOpts(ctypes.Structure):
     _fields_ = [("timeout_s", ctypes.c_double), ("withhold_stage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stage_ns", ctypes.c_void_p)]
+                ("block_threads", ctypes.c_int32), ("stage_ns", ctypes.c_void_p)]
 
 
 CHAIN_STAGES = ("analysis", "binning", "symbolic", "scan sums", "scan apply", "numeric")
@@ -350,10 +350,11 @@ class Chain:
     step may read an earlier step's outputs.  launch() enqueues (capturable
     in a CUDA graph), check() waits and raises SpgemmError(TIMEOUT) when a
     barrier wait expired.  With record_stages, every launch records when
-    block 0 passed each barrier; stage_ms() returns the stage durations."""
+    block 0 passed each barrier; stage_ms() returns the stage durations.
+    block_threads: 0 (768) or 1024 (spgemm_chain_opts.block_threads)."""
 
     def __init__(self, steps, timeout_s: float = 0.0, withhold_stage: int = -1,
-                 record_stages: bool = False):
+                 record_stages: bool = False, block_threads: int = 0):
         self._steps = list(steps)
         dev = self._steps[0][1].device
         arr = (_ChainStep * len(self._steps))()
@@ -364,7 +365,7 @@ class Chain:
         self.ws = _workspace(_lib.spgemm_chain_workspace_size(len(self._steps)), dev)
         self.stamps = (torch.zeros(2 + 6 * len(self._steps), dtype=torch.int64, device=dev)
                        if record_stages else None)
-        opts = _ChainOpts(float(timeout_s), int(withhold_stage), 0,
+        opts = _ChainOpts(float(timeout_s), int(withhold_stage), int(block_threads),
                           None if self.stamps is None else self.stamps.data_ptr())
         h = ctypes.c_void_p()
         _check(_lib.spgemm_chain_create(len(self._steps), arr, ctypes.byref(opts),

@@ -38,8 +38,9 @@ def _outputs(sg, p, cap, idt, vdt):
     return rowptrC, colC, valC
 
 
-@pytest.mark.parametrize("scale,idt", [(12, np.int32), (11, np.int64)])
-def test_chain_single_product_with_dense_rows(sg, scale, idt):
+@pytest.mark.parametrize("scale,idt,threads", [(12, np.int32, 0), (11, np.int64, 0),
+                                               (12, np.int32, 1024), (11, np.int64, 1024)])
+def test_chain_single_product_with_dense_rows(sg, scale, idt, threads):
     import torch
     M = inputs.rmat(scale, seed=210 + scale, index_dtype=idt)
     dA = sg.to_device(M)
@@ -47,7 +48,7 @@ def test_chain_single_product_with_dense_rows(sg, scale, idt):
     assert sg.plan(dA, dA).info()["rows_dense"] > 0
     cap = int(oracle.row_flops(M, M).sum())
     rp, col, val = _outputs(sg, p, cap, dA.col.dtype, torch.float64)
-    ch = sg.Chain([(p, rp, cap, col, val)], record_stages=True)
+    ch = sg.Chain([(p, rp, cap, col, val)], record_stages=True, block_threads=threads)
     R = oracle.spgemm(M, M)
     for _ in range(2):
         col.fill_(-1)
@@ -153,3 +154,15 @@ def test_chain_timeout_when_a_stage_is_withheld(sg):
     R = oracle.spgemm(M, M)
     assert_pattern_equal(C, R)
     assert np.array_equal(C.to_host()[2], R.val)
+
+
+def test_chain_rejects_other_block_sizes(sg):
+    import torch
+    M = inputs.rmat(8, seed=3)
+    dA = sg.to_device(M)
+    p = sg.device_plan([dA], [dA], max_row_nnz=8192)
+    cap = int(oracle.row_flops(M, M).sum())
+    rp, col, val = _outputs(sg, p, cap, dA.col.dtype, torch.float64)
+    with pytest.raises(sg.SpgemmError) as ei:
+        sg.Chain([(p, rp, cap, col, val)], block_threads=512)
+    assert ei.value.status == 1                     # SPGEMM_ERR_INVALID_ARG
