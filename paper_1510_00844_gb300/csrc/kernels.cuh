@@ -208,14 +208,14 @@ __device__ __forceinline__ long long row_end(const int64_t* rp, const int64_t* r
 }
 
 // ----------------------------------------------------------------- K1: flops
-// One warp per global row: flops_i, its class, per-class counts, total and
-// max flops, longest dense row; a product whose dense rows need more columns
-// than the shared-memory bitmap holds is flagged.
+// Per global row (a warp per tile of 32 rows): flops_i, its class, per-class
+// counts, total and max flops, longest dense row; a product whose dense rows
+// need more columns than the shared-memory bitmap holds is flagged.
 // Learned sizing (not in the paper): when `prm` is given, the warp also
-// evaluates the row-size predictor on the row's features (one lane per hidden
-// unit), writes the predicted capacity cap_out[r] = clamp(2^(y + margin) - 1,
-// max_k |B(k,:)|, min(flops, n)), and bins rows of at most dense_min products
-// by that capacity instead of by their flops.
+// evaluates the row-size predictor on each row's features (one lane per
+// hidden unit), writes the predicted capacity cap_out[r] = clamp(2^(y +
+// margin) - 1, max_k |B(k,:)|, min(flops, n)), and bins rows of at most
+// dense_min products by that capacity instead of by their flops.
 constexpr int kSizerF = 6;
 
 template <class IT>
@@ -245,113 +245,90 @@ __device__ __forceinline__ void analyze_kernel_body(long long R, const ProdDesc*
     const long long warp = ((long long)vbid * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)vnb * blockDim.x) >> 5;
     unsigned long long my_total = 0, my_max = 0;
-    if (!prm) {
-        // Tiles of 32 rows: a row of at most 32 A entries is summed by its
-        // own lane (eight entries' loads in flight at a time); longer rows
-        // by the whole warp, one after another.
-        for (long long tile = warp; tile * 32 < R; tile += nwarps) {
-            const long long r = tile * 32 + lane;
-            const bool in = r < R;
-            RowCtx<IT, NoVal> c{};
-            if (in) c = row_ctx<IT, NoVal>(D, rb, nprod, r);
-            const long long d = in ? c.a1 - c.a0 : 0;
-            long long f = 0, mx = 0;
-            if (in && d <= 32) {
-                for (long long p0 = c.a0; p0 < c.a1; p0 += 8) {
-                    long long k[8];
+    // Tiles of 32 rows: a row of at most 32 A entries is summed by its own
+    // lane (eight entries' loads in flight at a time); longer rows by the
+    // whole warp, one after another.  The predictor then runs row by row with
+    // a lane per hidden unit.
+    for (long long tile = warp; tile * 32 < R; tile += nwarps) {
+        const long long r = tile * 32 + lane;
+        const bool in = r < R;
+        RowCtx<IT, NoVal> c{};
+        if (in) c = row_ctx<IT, NoVal>(D, rb, nprod, r);
+        const long long d = in ? c.a1 - c.a0 : 0;
+        long long f = 0, mx = 0;
+        if (in && d <= 32) {
+            for (long long p0 = c.a0; p0 < c.a1; p0 += 8) {
+                long long k[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) k[u] = p0 + u < c.a1 ? (long long)c.ciA[p0 + u] : -1;
+                for (int u = 0; u < 8; ++u) k[u] = p0 + u < c.a1 ? (long long)c.ciA[p0 + u] : -1;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (k[u] >= 0) {
-                            const long long len = c.rpB[k[u] + 1] - c.rpB[k[u]];
-                            f += len;
-                            mx = len > mx ? len : mx;
-                        }
+                for (int u = 0; u < 8; ++u) {
+                    if (k[u] >= 0) {
+                        const long long len = c.rpB[k[u] + 1] - c.rpB[k[u]];
+                        f += len;
+                        mx = len > mx ? len : mx;
                     }
                 }
             }
-            for (unsigned lm = __ballot_sync(kFull, in && d > 32); lm; lm &= lm - 1u) {
-                const int src = __ffs(lm) - 1;
-                const RowCtx<IT, NoVal> cs = row_ctx<IT, NoVal>(D, rb, nprod, tile * 32 + src);
-                long long fs = 0, ms = 0;
-                for (long long p = cs.a0 + lane; p < cs.a1; p += 32) {
-                    const long long k = (long long)cs.ciA[p];
-                    const long long len = cs.rpB[k + 1] - cs.rpB[k];
-                    fs += len;
-                    ms = len > ms ? len : ms;
-                }
-                fs = warp_sum(fs);
-                ms = warp_max(ms);
-                if (lane == src) {
-                    f = fs;
-                    mx = ms;
-                }
-            }
-            int cl = -1 - lane;
-            if (in) {
-                flops_out[r] = f;
-                if (cap_out) cap_out[r] = f;
-                cl = row_class(f, dense_min, hash_shift);
-                cls_out[r] = (unsigned char)cl;
-                if (cl >= kClassDense0) {
-                    if (c.n > max_dense_n) blk_unsup = 1;
-                    atomicMax(&blk_dlen, (unsigned long long)d);
-                }
-                my_total += (unsigned long long)f;
-                if ((unsigned long long)f > my_max) my_max = (unsigned long long)f;
-            }
-            // one shared atomic per class present in the tile
-            const unsigned grp = __match_any_sync(kFull, cl);
-            if (in && (grp & lanemask_lt()) == 0u) atomicAdd(&hist[cl], (unsigned long long)__popc(grp));
         }
-        my_total = warp_sum(my_total);
-        my_max = warp_max(my_max);
-    }
-    for (long long r = prm ? warp : R; r < R; r += nwarps) {
-        const RowCtx<IT, NoVal> c = row_ctx<IT, NoVal>(D, rb, nprod, r);
-        long long f = 0, mx = 0;
-        for (long long p = c.a0 + lane; p < c.a1; p += 32) {
-            long long k = (long long)c.ciA[p];
-            const long long len = c.rpB[k + 1] - c.rpB[k];
-            f += len;
-            mx = len > mx ? len : mx;
+        for (unsigned lm = __ballot_sync(kFull, in && d > 32); lm; lm &= lm - 1u) {
+            const int src = __ffs(lm) - 1;
+            const RowCtx<IT, NoVal> cs = row_ctx<IT, NoVal>(D, rb, nprod, tile * 32 + src);
+            long long fs = 0, ms = 0;
+            for (long long p = cs.a0 + lane; p < cs.a1; p += 32) {
+                const long long k = (long long)cs.ciA[p];
+                const long long len = cs.rpB[k + 1] - cs.rpB[k];
+                fs += len;
+                ms = len > ms ? len : ms;
+            }
+            fs = warp_sum(fs);
+            ms = warp_max(ms);
+            if (lane == src) {
+                f = fs;
+                mx = ms;
+            }
         }
-        f = warp_sum(f);
-        mx = warp_max(mx);
         long long cap = 0;
-        if (prm && f > 0) {
-            const long long d = c.a1 - c.a0;
-            const long long ub = f < c.n ? f : c.n;
-            float x[kSizerF];
-            x[0] = log2f(1.f + (float)f);
-            x[1] = log2f(1.f + (float)d);
-            x[2] = log2f(1.f + (float)mx);
-            x[3] = log2f(1.f + (float)c.n);
-            x[4] = log2f(1.f + (float)f / (float)d);
-            x[5] = log2f(1.f + (float)ub);
+        if (prm) {
             const float* W1 = sp;
             const float* b1 = W1 + 32 * kSizerF;
             const float* W2 = b1 + 32;
             const float* b2 = W2 + 32 * 32;
             const float* w3 = b2 + 32;
-            float z = b1[lane];
-            for (int q = 0; q < kSizerF; ++q) z = __fadd_rn(z, __fmul_rn(W1[lane * kSizerF + q], x[q]));
-            const float h1 = z > 0.f ? z : 0.f;
-            float z2 = b2[lane];
-            for (int k = 0; k < 32; ++k)
-                z2 = __fadd_rn(z2, __fmul_rn(W2[lane * 32 + k], __shfl_sync(kFull, h1, k)));
-            const float h2 = z2 > 0.f ? z2 : 0.f;
-            const float y = warp_sum(__fmul_rn(w3[lane], h2)) + w3[32];
-            const float est = exp2f(y + margin) - 1.f;
-            cap = est >= (float)ub ? ub : (long long)ceilf(est > 0.f ? est : 0.f);
-            if (cap < mx) cap = mx;
-            if (cap > ub) cap = ub;
+            for (unsigned pm = __ballot_sync(kFull, in && f > 0); pm; pm &= pm - 1u) {
+                const int j = __ffs(pm) - 1;
+                const long long fj = __shfl_sync(kFull, f, j);
+                const long long dj = __shfl_sync(kFull, d, j);
+                const long long mj = __shfl_sync(kFull, mx, j);
+                const long long nj = __shfl_sync(kFull, c.n, j);
+                const long long ub = fj < nj ? fj : nj;
+                float x[kSizerF];
+                x[0] = log2f(1.f + (float)fj);
+                x[1] = log2f(1.f + (float)dj);
+                x[2] = log2f(1.f + (float)mj);
+                x[3] = log2f(1.f + (float)nj);
+                x[4] = log2f(1.f + (float)fj / (float)dj);
+                x[5] = log2f(1.f + (float)ub);
+                float z = b1[lane];
+                for (int q = 0; q < kSizerF; ++q) z = __fadd_rn(z, __fmul_rn(W1[lane * kSizerF + q], x[q]));
+                const float h1 = z > 0.f ? z : 0.f;
+                float z2 = b2[lane];
+                for (int k = 0; k < 32; ++k)
+                    z2 = __fadd_rn(z2, __fmul_rn(W2[lane * 32 + k], __shfl_sync(kFull, h1, k)));
+                const float h2 = z2 > 0.f ? z2 : 0.f;
+                const float y = warp_sum(__fmul_rn(w3[lane], h2)) + w3[32];
+                const float est = exp2f(y + margin) - 1.f;
+                long long cj = est >= (float)ub ? ub : (long long)ceilf(est > 0.f ? est : 0.f);
+                if (cj < mj) cj = mj;
+                if (cj > ub) cj = ub;
+                if (lane == j) cap = cj;
+            }
         }
-        if (lane == 0) {
+        int cl = -1 - lane;
+        if (in) {
             flops_out[r] = f;
             if (cap_out) cap_out[r] = prm ? cap : f;
-            int cl = row_class(f, dense_min, hash_shift);
+            cl = row_class(f, dense_min, hash_shift);
             if (prm && cl > kClassEmpty && cl < kClassDense0) {
                 cl = row_class(cap > 0 ? cap : 1, dense_min, hash_shift);
                 // bin 0 is the short-row path (one product per lane): a row
@@ -361,13 +338,17 @@ __device__ __forceinline__ void analyze_kernel_body(long long R, const ProdDesc*
             cls_out[r] = (unsigned char)cl;
             if (cl >= kClassDense0) {
                 if (c.n > max_dense_n) blk_unsup = 1;
-                atomicMax(&blk_dlen, (unsigned long long)(c.a1 - c.a0));
+                atomicMax(&blk_dlen, (unsigned long long)d);
             }
-            atomicAdd(&hist[cl], 1ull);
             my_total += (unsigned long long)f;
             if ((unsigned long long)f > my_max) my_max = (unsigned long long)f;
         }
+        // one shared atomic per class present in the tile
+        const unsigned grp = __match_any_sync(kFull, cl);
+        if (in && (grp & lanemask_lt()) == 0u) atomicAdd(&hist[cl], (unsigned long long)__popc(grp));
     }
+    my_total = warp_sum(my_total);
+    my_max = warp_max(my_max);
     if (lane == 0) {
         atomicAdd(&blk_total, my_total);
         atomicMax(&blk_max, my_max);
@@ -744,6 +725,9 @@ __device__ __forceinline__ void symbolic_dense_kernel_body(const ProdDesc* __res
                 long long j[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) j[t] = valid[t] ? (long long)ciB[q[t]] : -1;
+                // one shared atomic per product: OR-ing the lanes' bits of a
+                // common word first (a segmented scan, or __match_any_sync with
+                // __reduce_or_sync) was measured 3x and 5x slower
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
                     if (j[t] >= 0) atomicOr(&bm[j[t] >> 5], 1u << (j[t] & 31));

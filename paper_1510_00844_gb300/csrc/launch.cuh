@@ -47,8 +47,8 @@ cudaError_t launch_analyze(Plan& P) {
     if (P.R <= 0) return cudaSuccess;
     auto k = analyze_kernel<IT>;
     int occ = occupancy_blocks(k, 256, 0);
-    // a warp per row with the predictor, else a warp per tile of 32 rows
-    long long g = grid_for(P.R, P.prm ? 8 : 256, P.sm_count, occ);
+    // a warp per tile of 32 rows
+    long long g = grid_for(P.R, 256, P.sm_count, occ);
     count_launches(1);
     k<<<(unsigned)g, 256, 0, P.stream>>>(P.R, P.d_descs, P.rb, P.nprod, P.max_dense_n,
                                            P.dense_min, P.flops, P.cls, P.cnt, P.prm, P.margin,
