@@ -38,3 +38,57 @@ def test_rmat18_every_row_streamed_by_panel():
         del C, R
         torch.cuda.empty_cache()
     assert total == 2_958_724_919
+
+
+_K1 = np.int64(-7046029254386353131)    # odd 64-bit multipliers of the row hash
+_K2 = np.int64(-4417276706812531889)
+
+
+def _row_hashes_host(R):
+    """Per-row wrapping sums of col*K1 + bits(val)*K2 (int64 arithmetic)."""
+    with np.errstate(over="ignore"):
+        h = R.col.astype(np.int64) * _K1 + R.val.view(np.int64) * _K2
+        cs = np.concatenate([np.zeros(1, dtype=np.int64), np.cumsum(h, dtype=np.int64)])
+    return cs[R.rowptr[1:]] - cs[R.rowptr[:-1]]
+
+
+def _row_hashes_device(torch, C):
+    h = C.col.to(torch.int64) * int(_K1) + C.val.view(torch.int64) * int(_K2)
+    cs = torch.cat([torch.zeros(1, dtype=torch.int64, device=h.device), torch.cumsum(h, 0)])
+    return (cs[C.rowptr[1:]] - cs[C.rowptr[:-1]]).cpu().numpy()
+
+
+def test_rmat20_panels_every_row_hashed():
+    """The learned-sizing workload's product (R-MAT scale 20, whose C of 298 GB
+    exceeds HBM) in 32 row panels through the exact two-phase path; four of
+    the panels (the one with the most products and three seeded ones) have
+    every row compared with the oracle's: row counts exactly, and a 64-bit
+    hash of each row's (column, value bits) pairs."""
+    import torch
+    from paper_1510_00844_gb300 import spgemm as sg
+    A = inputs.rmat(20)
+    dA = sg.to_device(A)
+    rp = np.asarray(A.rowptr)
+    npan = 32
+    bounds = [((A.nrows * p) // npan, (A.nrows * (p + 1)) // npan) for p in range(npan)]
+    fl = oracle.row_flops(A, A)
+    pfl = np.array([fl[a:b].sum() for a, b in bounds])
+    pick = sorted({int(np.argmax(pfl))} | set(np.random.default_rng(20).choice(npan, 3, replace=False).tolist()))
+    total = 0
+    for p in pick:
+        a, b = bounds[p]
+        view = sg.DeviceCSR(b - a, A.ncols, dA.rowptr[a:b], dA.col, dA.val,
+                            rowend=dA.rowptr[a + 1:b + 1])
+        C = sg.spgemm(view, dA, verify=True)
+        sub = inputs.CSR(b - a, A.ncols, rp[a:b + 1] - rp[a], A.col[rp[a]:rp[b]],
+                         A.val[rp[a]:rp[b]])
+        R = oracle.spgemm(sub, A)
+        assert np.array_equal(C.rowptr.cpu().numpy(), R.rowptr), f"panel {p}: row counts differ"
+        hd = _row_hashes_device(torch, C)
+        hh = _row_hashes_host(R)
+        bad = np.nonzero(hd != hh)[0]
+        assert bad.size == 0, f"panel {p}: rows {bad[:8] + a} differ"
+        total += R.nnz
+        del C, R
+        torch.cuda.empty_cache()
+    assert total > 0
