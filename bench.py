@@ -117,12 +117,13 @@ def algorithmic_bytes(A, nnz_c: int):
 
 def dense_kernel_digest():
     """sha256 (first 16 hex) of the numeric_dense_kernel source: from its
-    section comment to the next section comment of kernels.cuh."""
+    section comment of kernels.cuh to the end of its kernel wrapper (the
+    learned path's packing kernel that follows is not part of it)."""
     import hashlib
     src = os.path.join(ROOT, "paper_1510_00844_gb300", "csrc", "kernels.cuh")
     text = open(src).read()
     a = text.index("// --------------------------------------------------- numeric: dense rows")
-    b = text.index("// ------------------------------------------------------------ k-slices", a)
+    b = text.index("// Learned sizing: close the gaps a slot-mode dense row leaves", a)
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
@@ -925,6 +926,24 @@ def run_profile_leg(args):
             ch.launch()
             ch.check()
         print(f"batched chain {len(pairs)} ER products: nnz {int(rp[-1].item())}", flush=True)
+    elif leg == "learned":
+        # one 1/16 row panel of the R-MAT 20 squaring, exact two-phase then
+        # learned sizing (the panels of the learned-sizing leg)
+        params, _ = train_sizer(sg, torch, inputs)
+        A = inputs.rmat(20)
+        dA = sg.to_device(A)
+        a, b = 0, A.nrows // 16
+        v = sg.DeviceCSR(b - a, A.ncols, dA.rowptr[a:b], dA.col, dA.val,
+                         rowend=dA.rowptr[a + 1:b + 1])
+        for _ in range(reps):
+            C = sg.spgemm(v, dA)
+            torch.cuda.synchronize()
+            nnz = C.nnz
+            del C
+            L, st = sg.learned_multiply(v, dA, params, 0.35)
+            torch.cuda.synchronize()
+            del L
+        print(f"learned panel of R-MAT 20: nnz {nnz}, overflow rows {st['overflow_rows']}", flush=True)
     elif leg in ("amg", "amg-chain", "mis2"):
         N = 128
         dA0 = sg.to_device(inputs.laplacian_7pt(N))
@@ -963,7 +982,7 @@ def main():
     ap.add_argument("--no-paths", action="store_true",
                     help="skip the split / batched / AMG comparisons")
     ap.add_argument("--profile-leg", choices=["product", "kslice", "batched", "batched-chain",
-                                              "amg", "amg-chain", "mis2"],
+                                              "amg", "amg-chain", "mis2", "learned"],
                     help="run one workload --reps times without timing (for ncu captures)")
     ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of --profile-leg")
     ap.add_argument("--reps", type=int, default=2, help="runs of --profile-leg")

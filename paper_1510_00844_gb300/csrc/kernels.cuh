@@ -1597,20 +1597,30 @@ __global__ void dense_slot_pack_kernel(const ProdDesc* __restrict__ D,
             const long long src = start + span * seg_chunk(g0, P) / P;
             const long long len = unit_cnt[u0 + g];
             if (src != dst) {
-                // dst < src: a forward copy in steps of 32 never overwrites
-                // an entry before it is read
-                for (long long q = 0; q < len; q += 32) {
-                    IT cv{};
-                    V vv{};
-                    const bool ok = q + lane < len;
-                    if (ok) {
-                        cv = ciC[src + q + lane];
-                        if constexpr (HV) vv = vC[src + q + lane];
+                // dst < src: a forward copy in steps of 128 entries (all of a
+                // step read before any is written) never overwrites an entry
+                // before it is read; four loads per lane are in flight
+                for (long long q = 0; q < len; q += 128) {
+                    IT cv[4];
+                    V vv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const long long x = q + 32 * t + lane;
+                        cv[t] = IT{};
+                        vv[t] = V{};
+                        if (x < len) {
+                            cv[t] = ciC[src + x];
+                            if constexpr (HV) vv[t] = vC[src + x];
+                        }
                     }
                     __syncwarp();
-                    if (ok) {
-                        ciC[dst + q + lane] = cv;
-                        if constexpr (HV) vC[dst + q + lane] = vv;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const long long x = q + 32 * t + lane;
+                        if (x < len) {
+                            ciC[dst + x] = cv[t];
+                            if constexpr (HV) vC[dst + x] = vv[t];
+                        }
                     }
                     __syncwarp();
                 }
