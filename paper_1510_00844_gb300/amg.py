@@ -23,12 +23,13 @@ class GalerkinChain:
     device-sized library calls (about 140 launches, captured in one graph).
     persistent=True: the transposes R_l^T (which depend only on the given
     R_l) are formed once here, and the six products run as one persistent
-    chain launch (spgemm_chain_launch): a graph of two nodes."""
+    chain launch (spgemm_chain_launch): a graph of two nodes; block_threads
+    is the chain's block size (1024 by default, for these short rows)."""
 
     def __init__(self, A0: sg.DeviceCSR, Rs: List[sg.DeviceCSR], stream: torch.cuda.Stream,
                  max_row_nnz: int = 64, tuning: Optional[sg.Tuning] = None,
                  persistent: bool = False, timeout_s: float = 0.0,
-                 record_stages: bool = False):
+                 record_stages: bool = False, block_threads: int = 1024):
         self.stream = stream
         self.persistent = persistent
         self.Rs = Rs
@@ -71,7 +72,7 @@ class GalerkinChain:
             # the hierarchy's rows are short (at most 56 products on a 7-point
             # stencil): 1024-thread blocks keep more of them in flight
             self.chain = sg.Chain(steps, timeout_s=timeout_s, record_stages=record_stages,
-                                  block_threads=1024)
+                                  block_threads=block_threads)
 
     def _transpose(self, lv):
         Rt = lv["Rt"]

@@ -65,9 +65,11 @@ def test_chain_single_product_with_dense_rows(sg, scale, idt, threads):
     assert sum(ms for _, _, ms in st) > 0.0
 
 
-def test_chain_batch_matches_execute(sg):
+@pytest.mark.parametrize("threads", [0, 1024])
+def test_chain_batch_matches_execute(sg, threads):
     """A batch of uneven float32 products as one chain step and a Boolean
-    copy as a second step: bit-identical to spgemm_execute."""
+    copy as a second step: bit-identical to spgemm_execute, with either
+    block size."""
     import torch
     pairs = inputs.batched_er(40, nmin=256, nmax=8192)
     As = [sg.to_device(a) for a, _ in pairs]
@@ -75,7 +77,7 @@ def test_chain_batch_matches_execute(sg):
     cap = int(sg.batch_plan(As, Bs).info()["flops"])
     p = sg.device_plan(As, Bs, max_row_nnz=4096)
     rp, col, val = _outputs(sg, p, cap, As[0].col.dtype, torch.float32)
-    ch = sg.Chain([(p, rp, cap, col, val)])
+    ch = sg.Chain([(p, rp, cap, col, val)], block_threads=threads)
     ch.launch()
     ch.check()
     q = sg.device_plan(As, Bs, max_row_nnz=4096)
@@ -91,14 +93,14 @@ def test_chain_batch_matches_execute(sg):
     Bp = [sg.DeviceCSR(b.nrows, b.ncols, b.rowptr, b.col, None) for b in Bs]
     pb = sg.device_plan(Ap, Bp, semiring=sg.OR_AND, max_row_nnz=4096)
     rpb, colb, _ = _outputs(sg, pb, cap, As[0].col.dtype, None)
-    chb = sg.Chain([(pb, rpb, cap, colb, None)])
+    chb = sg.Chain([(pb, rpb, cap, colb, None)], block_threads=threads)
     chb.launch()
     chb.check()
     assert torch.equal(rpb, rp) and torch.equal(colb[:nnz], col[:nnz])
 
 
-@pytest.mark.parametrize("N,levels", [(32, 3), (128, 3)])
-def test_chain_galerkin_hierarchy(sg, N, levels):
+@pytest.mark.parametrize("N,levels,threads", [(32, 3, 768), (128, 3, 1024)])
+def test_chain_galerkin_hierarchy(sg, N, levels, threads):
     """R^T A then (R^T A) R on every level, six dependent products in one
     launch, replayed from a CUDA graph: the same bits as the launch-by-launch
     graph, and the closed form 4^l x Laplacian of the coarse grid."""
@@ -109,7 +111,7 @@ def test_chain_galerkin_hierarchy(sg, N, levels):
     dA0 = sg.to_device(A0)
     dRs = [sg.to_device(R) for R in Rs]
     s = torch.cuda.Stream()
-    pc = amg.GalerkinChain(dA0, dRs, s, persistent=True)
+    pc = amg.GalerkinChain(dA0, dRs, s, persistent=True, block_threads=threads)
     pc.capture()
     ref = amg.GalerkinChain(dA0, dRs, s)
     ref.capture()
