@@ -109,3 +109,32 @@ def test_sizer_record_checks_need_no_gpu(lib):
     assert lib.spgemm_sizer_load(rec, need.value - 1, 6, None, None) == 1      # truncated
     assert lib.spgemm_sizer_load(rec, need.value, 6, None, None) == 1          # hash mismatch
     assert lib.spgemm_sizer_load(rec, need.value, 7, None, None) == 1          # another F
+
+
+def test_chain_argument_errors_need_no_gpu(lib):
+    """spgemm_chain_create rejects bad arguments before any device access
+    (the workspace address below is never dereferenced)."""
+    from paper_1510_00844_gb300 import spgemm as sg
+    L = sg._lib
+    L.spgemm_chain_workspace_size.restype = ctypes.c_size_t
+    need = L.spgemm_chain_workspace_size(1)
+    assert need >= 256 and need % 256 == 0
+    steps = (sg._ChainStep * 1)()
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(1 << 20)            # 256-byte aligned, not memory
+    ok_opts = sg._ChainOpts(0.0, -1, 0, None)
+    # no steps
+    assert L.spgemm_chain_create(0, steps, ctypes.byref(ok_opts), fake, need, ctypes.byref(h)) == 1
+    # workspace too small / not aligned
+    assert L.spgemm_chain_create(1, steps, ctypes.byref(ok_opts), fake, need - 1,
+                                 ctypes.byref(h)) == 4
+    assert L.spgemm_chain_create(1, steps, ctypes.byref(ok_opts), ctypes.c_void_p((1 << 20) + 8),
+                                 need, ctypes.byref(h)) == 1
+    # negative timeout, unsupported block size, missing plan
+    bad_t = sg._ChainOpts(-1.0, -1, 0, None)
+    assert L.spgemm_chain_create(1, steps, ctypes.byref(bad_t), fake, need, ctypes.byref(h)) == 1
+    bad_b = sg._ChainOpts(0.0, -1, 512, None)
+    assert L.spgemm_chain_create(1, steps, ctypes.byref(bad_b), fake, need, ctypes.byref(h)) == 1
+    assert b"block_threads" in L.spgemm_last_error()
+    assert L.spgemm_chain_create(1, steps, ctypes.byref(ok_opts), fake, need, ctypes.byref(h)) == 1
+    assert b"plan" in L.spgemm_last_error()
