@@ -456,6 +456,8 @@ __device__ __forceinline__ int short_row_gather(const RowCtx<IT, V>& c,
         if (lane < nb) {
             const long long k = (long long)c.ciA[b + lane];
             lo = c.rpB[k];
+            // capped: more than 32 products in one B row already makes the
+            // row too long for this path, and keeps the scan in int range
             len = (int)min(c.rpB[k + 1] - lo, 33LL);
             if constexpr (VALS) a = load_val(c.vA, b + lane);
         }

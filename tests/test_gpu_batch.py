@@ -193,6 +193,25 @@ def test_product_to_host_in_panels(sg, panels, semiring):
     assert H2 is H and np.array_equal(H2.col[:H2.nnz].numpy(), C.col.cpu().numpy())
 
 
+def test_pinned_host_arrays(sg):
+    """pipeline.pinned_empty: page-locked (registered) host memory of the
+    requested size and type, usable as a copy target, released when freed."""
+    import gc
+    import torch
+    from paper_1510_00844_gb300 import pipeline
+    for dtype, numel in ((torch.float64, 1000), (torch.int32, 3), (torch.int64, 0)):
+        h = pipeline.pinned_empty(numel, dtype)
+        assert h.dtype == dtype and h.numel() == numel and h.is_contiguous()
+        assert numel == 0 or h.is_pinned()
+        if numel:
+            d = torch.arange(numel, device="cuda").to(dtype)
+            h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            assert torch.equal(h, d.cpu())
+        del h
+        gc.collect()
+
+
 def test_batch_captured_in_a_graph(sg):
     """A batch of uneven products as one device-sized plan captured in a CUDA
     graph: replays give the host-synced batch's result bit for bit."""
