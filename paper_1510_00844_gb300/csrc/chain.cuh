@@ -202,6 +202,7 @@ template <class IT, class K, int LOG2T, int BW>
 __device__ __forceinline__ void chain_sym_bin(const ChainProduct& c, int* err, long long bid,
                                               long long nb) {
     constexpr int WARPS = chain_bin_warps<K, NoVal, LOG2T, false, BW>();
+    static_assert(WARPS >= 1, "a hash bin's table must fit the shared-memory budget");
     const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
     if (threadIdx.x < WARPS * 32)
         symbolic_hash_kernel_body<IT, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
@@ -213,6 +214,7 @@ template <class IT, class V, class K, int LOG2T, int BW>
 __device__ __forceinline__ void chain_num_bin(const ChainProduct& c, IT* colC, V* valC, int* err,
                                               long long bid, long long nb) {
     constexpr int WARPS = chain_bin_warps<K, V, LOG2T, true, BW>();
+    static_assert(WARPS >= 1, "a hash bin's table must fit the shared-memory budget");
     const int cls = kClassHash0 + (LOG2T == 6 ? 0 : LOG2T == 8 ? 1 : LOG2T == 10 ? 2 : 3);
     if (threadIdx.x < WARPS * 32)
         numeric_hash_kernel_body<IT, V, LOG2T, WARPS>(c.D, c.rb, c.nprod, c.rows, c.cnt, cls,
