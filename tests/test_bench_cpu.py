@@ -39,5 +39,23 @@ def test_profile_leg_options_are_listed():
                          capture_output=True, text=True, timeout=120)
     assert out.returncode == 0
     assert "--profile-leg" in out.stdout and "--products" in out.stdout
-    for leg in ("product", "kslice", "batched", "amg", "mis2"):
+    for leg in ("product", "kslice", "batched", "batched-chain", "amg", "amg-chain", "mis2",
+                "learned"):
         assert leg in out.stdout
+
+
+def test_stage_report_sums_by_stage_and_product():
+    stages = [(-1, "clear", 0.5), (0, "analysis", 1.0), (0, "numeric", 2.0),
+              (1, "analysis", 3.0), (1, "numeric", 4.0)]
+    r = bench._stage_report(stages)
+    assert r["by_stage"] == {"clear": 0.5, "analysis": 4.0, "numeric": 6.0}
+    assert r["by_product"] == {"0": 3.0, "1": 7.0}
+
+
+def test_dense_kernel_digest_is_stored_with_the_traffic_figure():
+    # the profile's traffic figure is used only while the kernel source
+    # matches the digest recorded with it
+    digest = bench.dense_kernel_digest()
+    assert len(digest) == 16
+    text = open(os.path.join(ROOT, "profiles", "numeric_dense_rmat18.md")).read()
+    assert (f"`{digest}`" in text) == (bench.profiled_traffic() is not None)
