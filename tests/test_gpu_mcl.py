@@ -20,11 +20,11 @@ def sg():
     return spgemm
 
 
-@pytest.mark.parametrize("thr", [1e-4, 1e-2])
-def test_mcl_steps_match_oracle(sg, thr):
-    M = inputs.mcl_transition(10)
+@pytest.mark.parametrize("scale,steps,thr", [(10, 3, 1e-4), (10, 3, 1e-2), (14, 2, 1e-4)])
+def test_mcl_steps_match_oracle(sg, scale, steps, thr):
+    M = inputs.mcl_transition(scale)
     dM = sg.to_device(M)
-    for step in range(3):
+    for step in range(steps):
         hostM = oracle.OCSR(M.nrows, M.ncols, *dM.to_host())
         C = sg.spgemm(dM, dM)
         R = oracle.mcl_prune_renorm(oracle.spgemm(hostM, hostM), thr)
