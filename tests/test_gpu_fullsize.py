@@ -53,19 +53,31 @@ def _row_hashes_host(R):
 
 
 def _row_hashes_device(torch, C):
+    """The same hash of a device CSR, or of a CSR view whose rows span
+    [rowptr[i], rowend[i]) (the learned path's slot form)."""
     h = C.col.to(torch.int64) * int(_K1) + C.val.view(torch.int64) * int(_K2)
     cs = torch.cat([torch.zeros(1, dtype=torch.int64, device=h.device), torch.cumsum(h, 0)])
-    return (cs[C.rowptr[1:]] - cs[C.rowptr[:-1]]).cpu().numpy()
+    start = C.rowptr[:-1] if C.rowend is None else C.rowptr[:C.nrows]
+    end = C.rowptr[1:] if C.rowend is None else C.rowend
+    return (cs[end] - cs[start]).cpu().numpy()
 
 
 def test_rmat20_panels_every_row_hashed():
     """The learned-sizing workload's product (R-MAT scale 20, whose C of 298 GB
-    exceeds HBM) in 32 row panels through the exact two-phase path; four of
-    the panels (the one with the most products and three seeded ones) have
-    every row compared with the oracle's: row counts exactly, and a 64-bit
-    hash of each row's (column, value bits) pairs."""
+    exceeds HBM) in 32 row panels through the exact two-phase path and the
+    learned-sizing path; four of the panels (the one with the most products
+    and three seeded ones) have every row compared with the oracle's: row
+    counts exactly, and a 64-bit hash of each row's (column, value bits)
+    pairs, for both paths."""
     import torch
     from paper_1510_00844_gb300 import spgemm as sg
+    # a predictor trained briefly on small R-MAT products (its misses are
+    # re-run exactly, so its quality only moves the overflow count)
+    train = [sg.to_device(inputs.rmat(s, seed=300 + s)) for s in (13, 14, 15)]
+    X, T = sg.sizer_training_set([(t, t) for t in train])
+    params = sg.sizer_init(seed=3)
+    sg.sizer_train(X, T, params, steps=400, batch=1024, lr=3e-3, seed=4)
+    del train, X, T
     A = inputs.rmat(20)
     dA = sg.to_device(A)
     rp = np.asarray(A.rowptr)
@@ -88,7 +100,14 @@ def test_rmat20_panels_every_row_hashed():
         hh = _row_hashes_host(R)
         bad = np.nonzero(hd != hh)[0]
         assert bad.size == 0, f"panel {p}: rows {bad[:8] + a} differ"
+        del C
+        torch.cuda.empty_cache()
+        L, st = sg.learned_multiply(view, dA, params, 0.35)
+        lens = (L.rowend - L.rowptr[:L.nrows]) if L.rowend is not None else torch.diff(L.rowptr)
+        assert np.array_equal(lens.cpu().numpy(), np.diff(R.rowptr)), f"panel {p}: learned row counts"
+        bad = np.nonzero(_row_hashes_device(torch, L) != hh)[0]
+        assert bad.size == 0, f"panel {p}: learned rows {bad[:8] + a} differ"
         total += R.nnz
-        del C, R
+        del L, R
         torch.cuda.empty_cache()
     assert total > 0
