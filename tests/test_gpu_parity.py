@@ -325,3 +325,67 @@ def test_hypersparse_kslices(sg, c):
     E = sg.dcsr_expand(sg.spgemm(v, dA), ids, A.nrows)
     assert_pattern_equal(E, R)
     assert np.array_equal(E.to_host()[2], R.val)
+
+
+@pytest.mark.parametrize("idt", [np.int32, np.int64])
+def test_short_rows_over_many_a_entries(sg, idt):
+    """Rows of at most 32 products whose A entries are many, most of them
+    pointing at empty rows of B (the table-free short-row path gathers their
+    products over several batches of 32 A entries), rows of exactly 32
+    products, and rows whose 32 products all land in one column."""
+    rng = np.random.default_rng(41)
+    n = 300
+    # B rows 0..199 empty; 200..299 one entry in column 5; 300..399 one to
+    # three entries in random columns
+    rB, cB = [], []
+    for k in range(200, 300):
+        rB.append(k)
+        cB.append(5)
+    blen_r = rng.integers(1, 4, 100)
+    for k, c in zip(range(300, 400), blen_r):
+        cols = rng.choice(n, int(c), replace=False)
+        rB += [k] * len(cols)
+        cB += list(cols)
+    B = inputs.coo_to_csr(400, n, np.array(rB), np.array(cB), rng.random(len(rB)), idt)
+    blen = np.diff(B.rowptr)
+    rows_A, cols_A = [], []
+
+    def add(i, ks):
+        ks = sorted(set(int(k) for k in ks))
+        rows_A.extend([i] * len(ks))
+        cols_A.extend(ks)
+
+    for i in range(64):
+        empty = rng.choice(200, 70, replace=False)
+        if i < 16:          # a few products among many empty rows
+            add(i, list(empty) + list(rng.choice(np.arange(300, 400), 6, replace=False)))
+        elif i < 32:        # exactly 32 products
+            ks, left = [], 32
+            for k in rng.permutation(np.arange(300, 400)):
+                if blen[k] <= left:
+                    ks.append(k)
+                    left -= blen[k]
+                if left == 0:
+                    break
+            ks += list(range(200, 200 + left))      # one product each
+            add(i, list(empty) + ks)
+        elif i < 48:        # 32 products, all in column 5
+            add(i, list(empty) + list(rng.choice(np.arange(200, 300), 32, replace=False)))
+        else:               # half in column 5, half anywhere
+            ks = list(rng.choice(np.arange(200, 300), 12, replace=False))
+            ks += list(rng.choice(np.arange(300, 400), 5, replace=False))
+            add(i, list(empty) + ks)
+    A = inputs.coo_to_csr(64, 400, np.array(rows_A), np.array(cols_A), rng.random(len(rows_A)), idt)
+    fl = oracle.row_flops(A, B)
+    assert fl.max() <= 32 and (fl == 32).sum() >= 32 and np.diff(A.rowptr).min() > 32
+    C, R = check_product(sg, A, B)
+    assert np.array_equal(C.to_host()[2], R.val)
+    assert np.all(np.diff(R.rowptr)[32:48] == 1)
+    # the same rows in slot mode (learned sizing with an untrained predictor:
+    # slots too small are re-run exactly)
+    dA, dB = sg.to_device(A), sg.to_device(B)
+    L, _ = sg.learned_multiply(dA, dB, sg.sizer_init(seed=9), 0.0)
+    Lc = sg.compact(L)
+    assert np.array_equal(Lc.rowptr.cpu().numpy(), R.rowptr)
+    assert np.array_equal(Lc.col.cpu().numpy().astype(np.int64), R.col)
+    assert np.array_equal(Lc.val.cpu().numpy(), R.val)
